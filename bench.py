@@ -1,0 +1,368 @@
+"""Benchmark of the zd-tree k-NN path on GB300.
+
+One step = one pass of the whole hot path over the 3D clustered workload
+(n = 10,000,000 int32 points in [0, 2^20)^3 from 1,000 Gaussian clusters,
+L = 16, k = 10): Morton encode, radix sort, gather, canonical tree (leaves,
+internal nodes, boxes), then exact all-points k-NN with int32 ids and int64
+squared distances written for every point.  Inputs are resident in HBM when
+the timed region starts; L2 is flushed (256 MiB write) between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain C, OpenMP over queries) on the
+host cores on a bounded sample of the same workload.  Other workloads:
+--workload 2d-uniform | dynamic | batched | differentiable.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kNN queries/s + zd-tree build pts/s (3D n=1e7,k=10) and % HBM roofline; fwd+bwd/s"
+
+# Algorithmic bytes (declared before measuring).
+#   all-points k-NN, per query: 12 (own coordinates) + 4 (sorted position ->
+#   id) + 12 (amortized node / leaf data) + 4k (ids) + 8k (int64 d^2).
+#   build, per point: encode 20, histogram 8, radix passes 20 + 24 (P - 1),
+#   gather 28, split 8, boxes 12, nodes 0.25 * 48.
+def knn_bytes_per_query(k: int) -> int:
+    return 12 + 4 + 12 + 12 * k
+
+
+def build_bytes_per_point(passes: int = 8) -> int:
+    return 20 + 8 + (20 + 24 * (passes - 1)) + 28 + 8 + 12 + 12
+
+
+def peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def hbm_peak():
+    p = peaks()
+    if "hbm_gbs" in p:
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_digest(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+KNN_SOURCES = ["paper_2111_04182_gb300/csrc/knn_impl.cuh", "paper_2111_04182_gb300/csrc/knn_i32.cu"]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None when absent or when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "knn_allpoints_3d_clustered.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+source:\s*([0-9a-f]+)\s+kernel:\s*(\S+)\s+workload:\s*(\S+)",
+                  text)
+    if not m or m.group(3) != kernel or m.group(4) != workload:
+        return None
+    if m.group(2) != source_digest(KNN_SOURCES):
+        return None
+    return int(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(2)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_04182_gb300 import datagen, zd
+
+    if args.workload != "3d-clustered":
+        return run_other(args, ws, rank, local)
+
+    w = datagen.workload_3d_clustered(n=args.n)
+    n, k, L, B = len(w["pts"]), w["k"], w["leaf_size"], w["coord_bits"]
+    pts_host = torch.from_numpy(w["pts"]).pin_memory()
+    pts = pts_host.to(dev)
+    idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((n, k), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(s)
+        t = zd.zd_build(pts, L, B)
+        if ev is not None:
+            ev[1].record(s)
+        t.knn(k, out=(idx, d2))
+        if ev is not None:
+            ev[2].record(s)
+        t.free()
+
+    for _ in range(args.warmup):
+        step()
+    st = zd.zd_check()
+    if st != 0:
+        raise RuntimeError("device status %d after warm-up" % st)
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        step(evs[i])
+        flush.zero_()  # L2 flush between steps, outside the step's events
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    st = zd.zd_check()
+    if st != 0:
+        raise RuntimeError("device status %d in the timed region" % st)
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    knn_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = sum(b + q for b, q in zip(build_ms, knn_ms)) / args.steps
+    step_ms = max_over_ranks(step_ms, ws)
+    value = ws * n / (step_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    idx_h = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    d2_h = torch.empty((n, k), dtype=torch.int64).pin_memory()
+
+    def e2e_step():
+        p = pts_host.to(dev, non_blocking=True)
+        t = zd.zd_build(p, L, B)
+        t.knn(k, out=(idx, d2))
+        idx_h.copy_(idx, non_blocking=True)
+        d2_h.copy_(d2, non_blocking=True)
+        t.free()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_steps = max(1, min(args.steps, 5))
+    barrier(ws)
+    e0.record(s)
+    for _ in range(e_steps):
+        e2e_step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e_steps, ws)
+
+    pk, pk_src = hbm_peak()
+    kb = knn_bytes_per_query(k) * n
+    knn_avg = sum(knn_ms) / len(knn_ms)
+    build_avg = sum(build_ms) / len(build_ms)
+    achieved = kb / (knn_avg / 1e3) / 1e9
+    traffic = profiled_traffic("k_knn", "3d-clustered-1e7") if n == 10_000_000 else None
+    bb = build_bytes_per_point() * n
+    launches_per_step = 20  # encode, plan, 8 sort passes, finish, gather, 5 topology, 2 id-table fills, knn
+    out = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "3d-clustered-1e7" if n == 10_000_000 else "3d-clustered-%d" % n,
+                   "n": n, "dim": 3, "k": k, "leaf_size": L, "coord_bits": B, "clusters": 1000,
+                   "step": "build + all-points k-NN (ids and int64 d^2 written)",
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "components": {"build_ms": build_avg, "build_pts_per_s": n / (build_avg / 1e3),
+                       "build_hbm_frac": bb / (build_avg / 1e3) / 1e9 / pk,
+                       "knn_ms": knn_avg, "knn_queries_per_s": n / (knn_avg / 1e3)},
+        "roofline": {"kernel": "k_knn<3,10,int>", "bound": "hbm", "achieved": achieved, "peak": pk,
+                     "peak_source": pk_src, "unit": "GB/s", "frac": achieved / pk,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": kb},
+        "clocks": clk,
+        "e2e": {"value": ws * n / (e2e_ms / 1e3), "unit": "queries/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": n * k * 12},
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, sample: int) -> dict:
+    """The oracle (plain C, OpenMP over queries) on the host cores: a full
+    build plus leaf-based k-NN for `sample` sorted positions, scaled to the
+    whole step."""
+    from oracle import oracle
+    pts, k, L, B = w["pts"], w["k"], w["leaf_size"], w["coord_bits"]
+    n = len(pts)
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    t = oracle.OracleTree(pts, L, B)
+    t_build = time.perf_counter() - t0
+    s = min(sample, n)
+    r0 = (n - s) // 2
+    t0 = time.perf_counter()
+    t.knn_sorted_range(k, r0, r0 + s, nthreads=cores)
+    t_knn = time.perf_counter() - t0
+    step = t_build + t_knn * n / s
+    return {"value": n / step, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": "full build of all %d points (1 thread) + leaf-based k-NN of %d consecutive sorted "
+                      "points (%d threads), k-NN time scaled by n/sample" % (n, s, cores),
+            "build_s": t_build, "knn_sample_s": t_knn}
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2111_04182_gb300 import datagen
+    if args.workload != "3d-clustered":
+        print(json.dumps({"impl": "reference", "unavailable": "reference arm is timed on the 3d-clustered workload only"}))
+        return
+    w = datagen.workload_3d_clustered(n=args.n)
+    n = len(w["pts"])
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    vals = []
+    for _ in range(args.steps):
+        cb = cpu_baseline(w, args.cpu_sample)
+        vals.append(cb["value"])
+    value = float(np.median(vals))
+    cb["value"] = value
+    out = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": n / value * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": "3d-clustered-1e7" if n == 10_000_000 else "3d-clustered-%d" % n,
+                      "n": n, "dim": 3, "k": w["k"], "leaf_size": w["leaf_size"]},
+           "impl": "reference", "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_other(args, ws, rank, local):
+    from bench_workloads import run_workload  # noqa: E402
+    out = run_workload(args)
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d-clustered")
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=300_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -60,7 +60,7 @@ def _load():
         lib.zdo_root.argtypes = [vp]
         lib.zdo_root.restype = i64
         lib.zdo_export.argtypes = [vp] + [vp] * 12
-        lib.zdo_knn.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, i32]
+        lib.zdo_knn.argtypes = [vp, vp, vp, i64, i32, i32, i64, i64, vp, vp, vp, i32]
         lib.zdo_knn_brute.argtypes = [vp, vp, vp, i64, vp, vp, vp, i64, i32, i32, vp, vp, vp, i32]
         lib.zdo_knn_dist_grad.argtypes = [vp, vp, vp, i64, i64, i32, i32, vp, i32, vp, vp]
         lib.zdo_knn_dist_grad.restype = f64
@@ -193,6 +193,19 @@ class OracleTree:
         return dict(ids=e["ids"], keys=e["keys"], lo=e["lo"][order], hi=e["hi"][order],
                     bit=e["bit"][order], box_lo=e["box_lo"][order], box_hi=e["box_hi"][order])
 
+    def knn_sorted_range(self, k: int, r0: int, r1: int, nthreads: int = 0):
+        """Leaf-based k-NN (Alg. 3) of the points at sorted positions [r0, r1)
+        only: rows in sorted order.  Used to time a bounded sample."""
+        lib = _load()
+        m = r1 - r0
+        idx = np.empty((m, k), np.int32)
+        d2 = None if self.is_float else np.empty((m, k), np.int64)
+        d2f = np.empty((m, k), np.float64) if self.is_float else None
+        st = lib.zdo_knn(self._h, None, None, m, k, MODE_LEAF, r0, r1, _p(idx), _p(d2), _p(d2f), nthreads)
+        if st:
+            raise OracleError(st)
+        return idx, (d2f if self.is_float else d2)
+
     def knn(self, k: int, queries=None, mode: int = MODE_LEAF, nthreads: int = 0):
         """k-NN by the tree.  queries=None: all points (Alg. 3 from each point's
         own leaf, self excluded), rows returned in id order when the ids are
@@ -204,7 +217,8 @@ class OracleTree:
             idx = np.empty((m, k), np.int32)
             d2 = None if self.is_float else np.empty((m, k), np.int64)
             d2f = np.empty((m, k), np.float64) if self.is_float else None
-            st = lib.zdo_knn(self._h, None, None, m, k, MODE_LEAF, _p(idx), _p(d2), _p(d2f), nthreads)
+            st = lib.zdo_knn(self._h, None, None, m, k, MODE_LEAF, 0, -1, _p(idx), _p(d2), _p(d2f),
+                             nthreads)
             if st:
                 raise OracleError(st)
             dist = d2f if self.is_float else d2
@@ -224,7 +238,7 @@ class OracleTree:
         d2 = None if self.is_float else np.empty((m, k), np.int64)
         d2f = np.empty((m, k), np.float64) if self.is_float else None
         st = lib.zdo_knn(self._h, None if self.is_float else _p(q), _p(q) if self.is_float else None,
-                         m, k, mode, _p(idx), _p(d2), _p(d2f), nthreads)
+                         m, k, mode, 0, -1, _p(idx), _p(d2), _p(d2f), nthreads)
         if st:
             raise OracleError(st)
         return idx, (d2f if self.is_float else d2)

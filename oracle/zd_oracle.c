@@ -602,20 +602,26 @@ static int64_t locate_leaf(const otree *t, uint64_t key)
 
 /* k-NN over the tree.
  *   mode 0: all points (leaf-based; queries are the tree's own points, self
- *           excluded by id; output row r belongs to sorted position r, whose
- *           id zdo_export reports);
+ *           excluded by id; output row r belongs to sorted position r0 + r,
+ *           whose id zdo_export reports; [r0, r1) selects a range of sorted
+ *           positions, r1 < 0 meaning all);
  *   mode 1: external queries, bit-based leaf location then Alg. 3;
  *   mode 2: external queries, root-based Alg. 2.
  * External queries come as q_i32 or q_f32 [m, dim].  Outputs [m, k]: ids
  * (-1 padding) and squared distances (int64, or fp64 in float mode; padding
  * INT64_MAX / +inf).  Returns ZDO_ERR_RANGE if a query key is out of range. */
 int zdo_knn(void *h, const int32_t *q_i32, const float *q_f32, int64_t m, int k, int mode,
-            int32_t *out_idx, int64_t *out_d2, double *out_d2f, int nthreads)
+            int64_t r0, int64_t r1, int32_t *out_idx, int64_t *out_d2, double *out_d2f,
+            int nthreads)
 {
     otree *t = (otree *)h;
     const int d = t->dim;
     if (k < 1 || (mode < 0 || mode > 2)) return ZDO_ERR_INVALID;
-    if (mode == 0) m = t->n;
+    if (mode == 0) {
+        if (r1 < 0 || r1 > t->n) r1 = t->n;
+        if (r0 < 0 || r0 > r1) return ZDO_ERR_INVALID;
+        m = r1 - r0;
+    }
     uint64_t *qkeys = NULL;
     if (mode == 1) {
         /* query Morton keys for the bit-based descent */
@@ -662,17 +668,18 @@ int zdo_knn(void *h, const int32_t *q_i32, const float *q_f32, int64_t m, int k,
             int64_t start = -1;
             int64_t row = r;
             if (mode == 0) {
-                /* r is a sorted position; its row is the point's id */
+                /* sorted position sp = r0 + r; self excluded by its id */
+                const int64_t sp = r0 + r;
                 for (int j = 0; j < d; ++j) {
-                    if (t->is_float) q.fc[j] = t->fcoord[r * d + j];
-                    else q.ic[j] = t->icoord[r * d + j];
+                    if (t->is_float) q.fc[j] = t->fcoord[sp * d + j];
+                    else q.ic[j] = t->icoord[sp * d + j];
                 }
-                q.self_id = t->ids[r];
-                /* the leaf that holds sorted position r */
+                q.self_id = t->ids[sp];
+                /* the leaf that holds sorted position sp */
                 int64_t v = t->root;
                 while (t->nodes[v].bit >= 0) {
                     const onode *x = &t->nodes[v];
-                    v = (r < t->nodes[x->left].hi) ? x->left : x->right;
+                    v = (sp < t->nodes[x->left].hi) ? x->left : x->right;
                 }
                 start = v;
             } else {

@@ -1,0 +1,674 @@
+// api.cu -- the C ABI of libzd (declared in include/zd.h): argument checks,
+// tree lifetime and memory, and the sequencing of the kernels of each step.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+using namespace zdk;
+
+// ------------------------------------------------------------ status word
+static __device__ u32 g_status;
+
+namespace zdk {
+u32 *status_word()
+{
+    static u32 *addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+        addr[dev] = (u32 *)p;
+    }
+    return addr[dev];
+}
+
+void *Mem::get(size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (a && a->alloc) {
+        p = a->alloc(bytes, (void *)s, a->ctx);
+    } else if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) failed = true;
+    return p;
+}
+
+void Mem::put(void *p, size_t bytes)
+{
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    if (a && a->release) a->release(p, bytes, (void *)s, a->ctx);
+    else cudaFreeAsync(p, s);
+}
+} // namespace zdk
+
+// ------------------------------------------------------------------- tree
+struct Block {
+    void *p;
+    size_t bytes;
+};
+
+struct zd_tree {
+    zd_params p;
+    zd_allocator alloc;
+    bool has_alloc;
+    int64_t n, cap, next_id, n_clouds;
+    int B;         // coordinate bits of the keys
+    int key_bits;  // significant key bits (Morton + cloud id)
+    int cloud_bit; // 64 for a single tree, dim * B for a forest
+    int is_float;
+    // device arrays
+    u64 *keys, *keys2;
+    int4 *pts, *pts2;
+    int *leaf_of, *leaf_lo, *meta;
+    int2 *ichild;
+    int *iparent, *ibit;
+    int2 *irange;
+    int4 *ibox;
+    int *lparent;
+    int4 *lbox;
+    int *counter;
+    double *frame;      // float trees: [n_clouds * 4]
+    int64_t *cloud_off; // forests: [n_clouds + 1]
+    u32 *alive;         // dynamic trees: per id, 1 = live, 2 = marked for delete
+    int64_t id_cap;
+    Block blocks[32];
+    int nblocks;
+};
+
+static Mem mem_of(const zd_tree *t, cudaStream_t s)
+{
+    Mem m;
+    m.a = t->has_alloc ? &t->alloc : nullptr;
+    m.s = s;
+    return m;
+}
+
+template <typename T>
+static bool tree_alloc(zd_tree *t, Mem &m, T **out, size_t count)
+{
+    size_t bytes = count * sizeof(T) + 16;
+    void *p = m.get(bytes);
+    *out = (T *)p;
+    if (!p) return false;
+    t->blocks[t->nblocks++] = Block{p, bytes};
+    return true;
+}
+
+static void tree_release(zd_tree *t, cudaStream_t s)
+{
+    Mem m = mem_of(t, s);
+    for (int i = 0; i < t->nblocks; ++i) m.put(t->blocks[i].p, t->blocks[i].bytes);
+    t->nblocks = 0;
+}
+
+static TreeView view_of(const zd_tree *t)
+{
+    TreeView v;
+    v.n = (int)t->n;
+    v.dim = t->p.dim;
+    v.coord_bits = t->B;
+    v.cloud_bit = t->cloud_bit;
+    v.keys = t->keys;
+    v.pts = t->pts;
+    v.leaf_of = t->leaf_of;
+    v.leaf_lo = t->leaf_lo;
+    v.meta = t->meta;
+    v.ichild = t->ichild;
+    v.iparent = t->iparent;
+    v.ibit = t->ibit;
+    v.irange = t->irange;
+    v.ibox = t->ibox;
+    v.lparent = t->lparent;
+    v.lbox = t->lbox;
+    v.cloud_off = t->cloud_off;
+    return v;
+}
+
+static TopoBuffers topo_of(zd_tree *t)
+{
+    TopoBuffers b;
+    b.leaf_of = t->leaf_of;
+    b.leaf_lo = t->leaf_lo;
+    b.meta = t->meta;
+    b.ichild = t->ichild;
+    b.iparent = t->iparent;
+    b.ibit = t->ibit;
+    b.irange = t->irange;
+    b.ibox = t->ibox;
+    b.lparent = t->lparent;
+    b.lbox = t->lbox;
+    b.counter = t->counter;
+    return b;
+}
+
+static int check_params(const zd_params *p)
+{
+    if (!p) return ZD_ERR_INVALID_ARG;
+    if (p->dim != 2 && p->dim != 3) return ZD_ERR_INVALID_ARG;
+    if (p->leaf_size < 1 || p->leaf_size > 256) return ZD_ERR_INVALID_ARG;
+    if (p->coord_type != ZD_COORD_I32 && p->coord_type != ZD_COORD_F32) return ZD_ERR_INVALID_ARG;
+    // coordinate differences must fit int32: B <= 31 (2D), 21 (3D)
+    const int bmax = p->dim == 3 ? 21 : 31;
+    if (p->coord_bits < 1 || p->coord_bits > bmax) return ZD_ERR_INVALID_ARG;
+    if (p->capacity < 0) return ZD_ERR_INVALID_ARG;
+    return ZD_OK;
+}
+
+static int ceil_log2(int64_t x)
+{
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
+}
+
+// Allocate every device array of a tree for `cap` points and `n_clouds`.
+static int tree_arrays(zd_tree *t, Mem &m, bool dynamic)
+{
+    const size_t cap = (size_t)std::max<int64_t>(t->cap, 1);
+    bool ok = tree_alloc(t, m, &t->keys, cap) && tree_alloc(t, m, &t->pts, cap) &&
+              tree_alloc(t, m, &t->leaf_of, cap) && tree_alloc(t, m, &t->leaf_lo, cap + 2) &&
+              tree_alloc(t, m, &t->meta, 4) && tree_alloc(t, m, &t->ichild, cap) &&
+              tree_alloc(t, m, &t->iparent, cap) && tree_alloc(t, m, &t->ibit, cap) &&
+              tree_alloc(t, m, &t->irange, cap) && tree_alloc(t, m, &t->ibox, 2 * cap) &&
+              tree_alloc(t, m, &t->lparent, cap + 1) && tree_alloc(t, m, &t->lbox, 2 * cap + 2) &&
+              tree_alloc(t, m, &t->counter, cap);
+    if (ok && t->is_float) ok = tree_alloc(t, m, &t->frame, 4 * (size_t)t->n_clouds);
+    if (ok && dynamic) {
+        ok = tree_alloc(t, m, &t->keys2, cap) && tree_alloc(t, m, &t->pts2, cap);
+    }
+    return ok ? ZD_OK : ZD_ERR_OOM;
+}
+
+static zd_tree *tree_new(const zd_params *p, const zd_allocator *alloc)
+{
+    zd_tree *t = (zd_tree *)calloc(1, sizeof(zd_tree));
+    if (!t) return nullptr;
+    t->p = *p;
+    if (alloc) {
+        t->alloc = *alloc;
+        t->has_alloc = true;
+    }
+    t->is_float = p->coord_type == ZD_COORD_F32;
+    return t;
+}
+
+// encode -> sort -> gather -> topology, shared by every build.
+static int build_core(zd_tree *t, const void *d_pts, const int64_t *seg_off, int64_t n_seg,
+                      int64_t max_seg, cudaStream_t s)
+{
+    Mem m = mem_of(t, s);
+    const int64_t n = t->n;
+    const int dim = t->p.dim;
+    const int npasses = (t->key_bits + RADIX_BITS - 1) / RADIX_BITS;
+    Scratch<u64> raw(m, n > 0 ? n : 1);
+    Scratch<int32_t> perm(m, n > 0 ? n : 1);
+    Scratch<u32> hist(m, MAX_PASSES * RADIX);
+    Scratch<int> mm(m, (size_t)6 * std::max<int64_t>(n_seg, 1));
+    if (!raw.p || !perm.p || !hist.p || !mm.p) return ZD_ERR_OOM;
+    ZD_CUDA(cudaMemsetAsync(hist.p, 0, MAX_PASSES * RADIX * sizeof(u32), s));
+    const int cloud_shift = seg_off ? t->cloud_bit : 0;
+    if (t->is_float) {
+        ZD_TRY(launch_float_frames((const float *)d_pts, n, dim, t->B, seg_off, n_seg, max_seg,
+                                   t->frame, mm.p, s));
+        ZD_TRY(launch_encode_f32((const float *)d_pts, n, dim, t->B, t->frame, seg_off, n_seg,
+                                 cloud_shift, raw.p, hist.p, npasses, s));
+    } else {
+        ZD_TRY(launch_encode_i32((const int32_t *)d_pts, n, dim, t->B, t->p.shift, seg_off, n_seg,
+                                 cloud_shift, raw.p, hist.p, npasses, s));
+    }
+    ZD_TRY(radix_sort(raw.p, n, t->key_bits, t->keys, perm.p, hist.p, m));
+    ZD_TRY(launch_gather(d_pts, dim, n, perm.p, t->keys, t->cloud_bit, t->cloud_off, 0, t->pts, s));
+    ZD_TRY(build_topology(t->keys, t->pts, n, t->p.leaf_size, dim, t->is_float, topo_of(t), m));
+    return m.failed ? ZD_ERR_OOM : ZD_OK;
+}
+
+__global__ void k_fill_u32(u32 *p, int64_t a, int64_t z, u32 v)
+{
+    for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < z;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+extern "C" {
+
+const char *zd_status_string(int status)
+{
+    switch (status) {
+    case ZD_OK: return "ok";
+    case ZD_ERR_INVALID_ARG: return "invalid argument";
+    case ZD_ERR_RANGE: return "coordinate outside [0, 2^coord_bits) after the shift";
+    case ZD_ERR_OOM: return "out of device memory";
+    case ZD_ERR_CUDA: return "CUDA runtime error";
+    case ZD_ERR_NOT_FOUND: return "id not live";
+    case ZD_ERR_DUPLICATE_ID: return "id repeated in one batch";
+    case ZD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case ZD_ERR_UNIMPLEMENTED: return "not implemented for these parameters";
+    case ZD_ERR_CAPACITY: return "tree capacity exceeded";
+    default: return "unknown status";
+    }
+}
+
+int zd_check(void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    ZD_CUDA(cudaStreamSynchronize(s));
+    u32 *w = status_word();
+    if (!w) return ZD_ERR_CUDA;
+    u32 v = 0;
+    ZD_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
+    if (v) {
+        u32 z = 0;
+        ZD_CUDA(cudaMemcpy(w, &z, sizeof(z), cudaMemcpyHostToDevice));
+    }
+    return (int)v;
+}
+
+int zd_morton_encode(const zd_params *p, const int32_t *d_pts, int64_t n, uint64_t *d_keys,
+                     void *stream)
+{
+    ZD_TRY(check_params(p));
+    if (p->coord_type != ZD_COORD_I32 || n < 0 || (n > 0 && (!d_pts || !d_keys)))
+        return ZD_ERR_INVALID_ARG;
+    if (!status_word()) return ZD_ERR_CUDA;
+    return launch_encode_i32(d_pts, n, p->dim, p->coord_bits, p->shift, nullptr, 0, 0,
+                             (u64 *)d_keys, nullptr, 0, (cudaStream_t)stream);
+}
+
+int zd_morton_sort(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t *d_keys_out,
+                   int32_t *d_perm_out, const zd_allocator *alloc, void *stream)
+{
+    if (n < 0 || key_bits < 1 || key_bits > 64) return ZD_ERR_INVALID_ARG;
+    if (n > 0 && (!d_keys_in || !d_keys_out || !d_perm_out)) return ZD_ERR_INVALID_ARG;
+    if (!status_word()) return ZD_ERR_CUDA;
+    Mem m;
+    m.a = alloc;
+    m.s = (cudaStream_t)stream;
+    int r = radix_sort((const u64 *)d_keys_in, n, key_bits, (u64 *)d_keys_out, d_perm_out, nullptr, m);
+    if (r == ZD_OK && m.failed) r = ZD_ERR_OOM;
+    return r;
+}
+
+int zd_build(const zd_params *p, const zd_allocator *alloc, const void *d_pts, int64_t n,
+             void *stream, zd_tree **out)
+{
+    if (!out) return ZD_ERR_INVALID_ARG;
+    *out = nullptr;
+    ZD_TRY(check_params(p));
+    if (n < 0 || n >= ((int64_t)1 << 31) - 2 || (n > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
+    if (p->capacity > 0 && p->capacity < n) return ZD_ERR_INVALID_ARG;
+    if (!status_word()) return ZD_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    zd_tree *t = tree_new(p, alloc);
+    if (!t) return ZD_ERR_OOM;
+    t->n = n;
+    t->cap = std::max<int64_t>(p->capacity, n);
+    t->next_id = n;
+    t->n_clouds = 1;
+    t->B = p->coord_bits;
+    t->key_bits = p->dim * p->coord_bits;
+    t->cloud_bit = 64;
+    const bool dynamic = !t->is_float;
+    Mem m = mem_of(t, s);
+    int r = tree_arrays(t, m, dynamic);
+    if (r == ZD_OK && dynamic) {
+        t->id_cap = std::max<int64_t>(t->cap, 1);
+        if (!tree_alloc(t, m, &t->alive, (size_t)t->id_cap)) r = ZD_ERR_OOM;
+        if (r == ZD_OK) {
+            k_fill_u32<<<grid_for(t->id_cap, 256, 4096), 256, 0, s>>>(t->alive, 0, t->id_cap, 0u);
+            k_fill_u32<<<grid_for(n, 256, 4096), 256, 0, s>>>(t->alive, 0, n, 1u);
+            if (cudaGetLastError() != cudaSuccess) r = ZD_ERR_CUDA;
+        }
+    }
+    if (r == ZD_OK) r = build_core(t, d_pts, nullptr, 1, n, s);
+    if (r != ZD_OK) {
+        tree_release(t, s);
+        free(t);
+        return r;
+    }
+    *out = t;
+    return ZD_OK;
+}
+
+int zd_build_batched(const zd_params *p, const zd_allocator *alloc, const void *d_pts,
+                     const int64_t *h_offsets, const int64_t *d_offsets, int64_t n_clouds,
+                     void *stream, zd_tree **out)
+{
+    if (!out) return ZD_ERR_INVALID_ARG;
+    *out = nullptr;
+    ZD_TRY(check_params(p));
+    if (n_clouds < 1 || n_clouds > 65535 || !h_offsets || !d_offsets) return ZD_ERR_INVALID_ARG;
+    if (h_offsets[0] != 0) return ZD_ERR_INVALID_ARG;
+    int64_t max_seg = 0;
+    for (int64_t c = 0; c < n_clouds; ++c) {
+        int64_t sz = h_offsets[c + 1] - h_offsets[c];
+        if (sz < 0) return ZD_ERR_INVALID_ARG;
+        max_seg = std::max(max_seg, sz);
+    }
+    const int64_t n = h_offsets[n_clouds];
+    if (n >= ((int64_t)1 << 31) - 2 || (n > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
+    const int cbits = ceil_log2(n_clouds);
+    const int B = std::min(p->coord_bits, (64 - cbits) / p->dim);
+    if (B < 1) return ZD_ERR_INVALID_ARG;
+    if (!status_word()) return ZD_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    zd_tree *t = tree_new(p, alloc);
+    if (!t) return ZD_ERR_OOM;
+    t->n = n;
+    t->cap = n;
+    t->next_id = 0;
+    t->n_clouds = n_clouds;
+    t->B = B;
+    t->cloud_bit = p->dim * B;
+    t->key_bits = t->cloud_bit + cbits;
+    Mem m = mem_of(t, s);
+    int r = tree_arrays(t, m, false);
+    if (r == ZD_OK && !tree_alloc(t, m, &t->cloud_off, (size_t)n_clouds + 1)) r = ZD_ERR_OOM;
+    if (r == ZD_OK && cudaMemcpyAsync(t->cloud_off, d_offsets, sizeof(int64_t) * (n_clouds + 1),
+                                      cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        r = ZD_ERR_CUDA;
+    if (r == ZD_OK) r = build_core(t, d_pts, t->cloud_off, n_clouds, max_seg, s);
+    if (r != ZD_OK) {
+        tree_release(t, s);
+        free(t);
+        return r;
+    }
+    *out = t;
+    return ZD_OK;
+}
+
+int zd_free(zd_tree *t, void *stream)
+{
+    if (!t) return ZD_OK;
+    tree_release(t, (cudaStream_t)stream);
+    free(t);
+    return ZD_OK;
+}
+
+int zd_tree_info_get(const zd_tree *t, zd_tree_info *out, void *stream)
+{
+    if (!t || !out) return ZD_ERR_INVALID_ARG;
+    int nl = 1;
+    ZD_CUDA(cudaMemcpyAsync(&nl, t->meta, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    ZD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    out->n = t->n;
+    out->capacity = t->cap;
+    out->next_id = t->next_id;
+    out->n_leaves = nl;
+    out->n_internal = nl - 1;
+    out->dim = t->p.dim;
+    out->leaf_size = t->p.leaf_size;
+    out->coord_bits = t->B;
+    out->coord_type = t->p.coord_type;
+    out->n_clouds = t->n_clouds;
+    return ZD_OK;
+}
+
+} // extern "C"
+
+// Export helpers: split int4 box pairs into [count, dim] corner arrays and
+// internal node ranges into lo / hi.
+__global__ void k_export_boxes(const int4 *box, const int *meta, int internal, int dim, int32_t *lo,
+                               int32_t *hi)
+{
+    const int count = internal ? meta[0] - 1 : meta[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        int4 a = box[2 * i], b = box[2 * i + 1];
+        int va[3] = {a.x, a.y, a.z}, vb[3] = {b.x, b.y, b.z};
+        for (int j = 0; j < dim; ++j) {
+            if (lo) lo[(int64_t)i * dim + j] = va[j];
+            if (hi) hi[(int64_t)i * dim + j] = vb[j];
+        }
+    }
+}
+
+__global__ void k_export_nodes(const int2 *irange, const int2 *ichild, const int *meta, int32_t *lo,
+                               int32_t *hi, int32_t *left, int32_t *right)
+{
+    const int count = meta[0] - 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        if (lo) lo[i] = irange[i].x;
+        if (hi) hi[i] = irange[i].y;
+        if (left) left[i] = ichild[i].x;
+        if (right) right[i] = ichild[i].y;
+    }
+}
+
+__global__ void k_export_ids(const int4 *pts, int64_t n, int32_t *ids)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        ids[i] = pts[i].w;
+}
+
+extern "C" int zd_export_tree(const zd_tree *t, int32_t *d_ids, uint64_t *d_keys, int32_t *d_leaf_lo,
+                              int32_t *d_node_lo, int32_t *d_node_hi, int32_t *d_node_bit,
+                              int32_t *d_node_left, int32_t *d_node_right, int32_t *d_node_parent,
+                              int32_t *d_leaf_parent, void *d_node_box_lo, void *d_node_box_hi,
+                              void *d_leaf_box_lo, void *d_leaf_box_hi, void *stream)
+{
+    if (!t) return ZD_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int nl = 1;
+    ZD_CUDA(cudaMemcpyAsync(&nl, t->meta, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ZD_CUDA(cudaStreamSynchronize(s));
+    const int64_t n = t->n;
+    if (d_ids && n > 0) k_export_ids<<<grid_for(n, 256, 4096), 256, 0, s>>>(t->pts, n, d_ids);
+    if (d_keys && n > 0)
+        ZD_CUDA(cudaMemcpyAsync(d_keys, t->keys, sizeof(u64) * n, cudaMemcpyDeviceToDevice, s));
+    if (d_leaf_lo)
+        ZD_CUDA(cudaMemcpyAsync(d_leaf_lo, t->leaf_lo, sizeof(int) * (nl + 1), cudaMemcpyDeviceToDevice, s));
+    if (nl > 1) {
+        k_export_nodes<<<grid_for(nl, 256, 4096), 256, 0, s>>>(t->irange, t->ichild, t->meta, d_node_lo,
+                                                              d_node_hi, d_node_left, d_node_right);
+        if (d_node_bit)
+            ZD_CUDA(cudaMemcpyAsync(d_node_bit, t->ibit, sizeof(int) * (nl - 1), cudaMemcpyDeviceToDevice, s));
+        if (d_node_parent)
+            ZD_CUDA(cudaMemcpyAsync(d_node_parent, t->iparent, sizeof(int) * (nl - 1),
+                                    cudaMemcpyDeviceToDevice, s));
+        if (d_node_box_lo || d_node_box_hi)
+            k_export_boxes<<<grid_for(nl, 256, 4096), 256, 0, s>>>(t->ibox, t->meta, 1, t->p.dim,
+                                                                  (int32_t *)d_node_box_lo,
+                                                                  (int32_t *)d_node_box_hi);
+    }
+    if (d_leaf_parent)
+        ZD_CUDA(cudaMemcpyAsync(d_leaf_parent, t->lparent, sizeof(int) * nl, cudaMemcpyDeviceToDevice, s));
+    if (d_leaf_box_lo || d_leaf_box_hi)
+        k_export_boxes<<<grid_for(nl, 256, 4096), 256, 0, s>>>(t->lbox, t->meta, 0, t->p.dim,
+                                                              (int32_t *)d_leaf_box_lo,
+                                                              (int32_t *)d_leaf_box_hi);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+// Encode, sort and gather external queries into Morton order.
+static int prepare_queries(const zd_tree *t, const void *d_q, int64_t m, const int64_t *seg_off,
+                           int64_t n_seg, Mem &mem, u64 *qkeys, int4 *q4)
+{
+    cudaStream_t s = mem.s;
+    const int npasses = (t->key_bits + RADIX_BITS - 1) / RADIX_BITS;
+    Scratch<u64> raw(mem, m);
+    Scratch<int32_t> perm(mem, m);
+    Scratch<u32> hist(mem, MAX_PASSES * RADIX);
+    if (!raw.p || !perm.p || !hist.p) return ZD_ERR_OOM;
+    ZD_CUDA(cudaMemsetAsync(hist.p, 0, MAX_PASSES * RADIX * sizeof(u32), s));
+    const int cloud_shift = seg_off ? t->cloud_bit : 0;
+    if (t->is_float)
+        ZD_TRY(launch_encode_f32((const float *)d_q, m, t->p.dim, t->B, t->frame, seg_off, n_seg,
+                                 cloud_shift, raw.p, hist.p, npasses, s));
+    else
+        ZD_TRY(launch_encode_i32((const int32_t *)d_q, m, t->p.dim, t->B, t->p.shift, seg_off, n_seg,
+                                 cloud_shift, raw.p, hist.p, npasses, s));
+    ZD_TRY(radix_sort(raw.p, m, t->key_bits, qkeys, perm.p, hist.p, mem));
+    ZD_TRY(launch_gather(d_q, t->p.dim, m, perm.p, qkeys, 64, nullptr, 0, q4, s));
+    return ZD_OK;
+}
+
+static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m, int k, int mode,
+                   int32_t *d_idx, void *d_dist, cudaStream_t s)
+{
+    KnnArgs a;
+    a.t = view_of(t);
+    a.k = k;
+    a.mode = mode;
+    a.is_float = t->is_float;
+    a.q = q4;
+    a.qkey = qkeys;
+    a.m = m;
+    a.out_idx = d_idx;
+    a.out_dist = d_dist;
+    return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s);
+}
+
+extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k, int mode,
+                      int32_t *d_idx, void *d_dist, void *stream)
+{
+    if (!t || !d_idx || k < 1) return ZD_ERR_INVALID_ARG;
+    if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
+    if (t->cloud_off) return ZD_ERR_INVALID_ARG; // forests: zd_knn_batched
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == ZD_SEARCH_LEAF) {
+        if (d_queries) return ZD_ERR_INVALID_ARG;
+        return run_knn(t, nullptr, nullptr, t->n, k, mode, d_idx, d_dist, s);
+    }
+    if (mode != ZD_SEARCH_BIT && mode != ZD_SEARCH_ROOT) return ZD_ERR_INVALID_ARG;
+    if (m < 0 || m >= ((int64_t)1 << 31) - 2 || (m > 0 && !d_queries)) return ZD_ERR_INVALID_ARG;
+    if (m == 0) return ZD_OK;
+    Mem mem = mem_of(t, s);
+    Scratch<u64> qkeys(mem, m);
+    Scratch<int4> q4(mem, m);
+    if (!qkeys.p || !q4.p) return ZD_ERR_OOM;
+    ZD_TRY(prepare_queries(t, d_queries, m, nullptr, 1, mem, qkeys.p, q4.p));
+    ZD_TRY(run_knn(t, q4.p, qkeys.p, m, k, mode, d_idx, d_dist, s));
+    return mem.failed ? ZD_ERR_OOM : ZD_OK;
+}
+
+extern "C" int zd_knn_batched(const zd_tree *t, const void *d_queries, const int64_t *d_query_offsets,
+                              int64_t m, int k, int32_t *d_idx, void *d_dist, void *stream)
+{
+    if (!t || !d_idx || k < 1) return ZD_ERR_INVALID_ARG;
+    if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
+    if (!t->cloud_off) return ZD_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!d_queries) return run_knn(t, nullptr, nullptr, t->n, k, ZD_SEARCH_LEAF, d_idx, d_dist, s);
+    if (!d_query_offsets || m < 0 || m >= ((int64_t)1 << 31) - 2) return ZD_ERR_INVALID_ARG;
+    if (m == 0) return ZD_OK;
+    Mem mem = mem_of(t, s);
+    Scratch<u64> qkeys(mem, m);
+    Scratch<int4> q4(mem, m);
+    if (!qkeys.p || !q4.p) return ZD_ERR_OOM;
+    ZD_TRY(prepare_queries(t, d_queries, m, d_query_offsets, t->n_clouds, mem, qkeys.p, q4.p));
+    ZD_TRY(run_knn(t, q4.p, qkeys.p, m, k, ZD_SEARCH_ROOT, d_idx, d_dist, s));
+    return mem.failed ? ZD_ERR_OOM : ZD_OK;
+}
+
+// --------------------------------------------------------------- updates
+namespace zdk {
+int update_insert(const TreeView &v, const u64 *keys, const int4 *pts, int64_t n, const void *d_pts,
+                  int64_t b, int dim, int B, const uint32_t *shift, int key_bits, int32_t next_id,
+                  u64 *keys_out, int4 *pts_out, u32 *alive, int32_t *d_new_ids, Mem &mem);
+int update_delete_mark(u32 *alive, int64_t id_cap, const int32_t *ids, int64_t b, Mem &mem,
+                       int *result);
+int update_delete_unmark(u32 *alive, int64_t id_cap, const int32_t *ids, int64_t b, cudaStream_t s);
+int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *alive, const int32_t *ids,
+                          int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem);
+} // namespace zdk
+
+extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t *d_new_ids, void *stream)
+{
+    if (!t || b < 0 || (b > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
+    if (t->cloud_off || t->is_float) return ZD_ERR_UNIMPLEMENTED;
+    if (b == 0) return ZD_OK;
+    if (t->n + b > t->cap) return ZD_ERR_CAPACITY;
+    if (t->next_id + b >= ((int64_t)1 << 31) - 2) return ZD_ERR_CAPACITY;
+    cudaStream_t s = (cudaStream_t)stream;
+    Mem mem = mem_of(t, s);
+    // grow the per-id liveness table if the new ids do not fit
+    if (t->next_id + b > t->id_cap) {
+        int64_t nc = std::max<int64_t>(2 * t->id_cap, t->next_id + b);
+        u32 *na = (u32 *)mem.get(sizeof(u32) * (size_t)nc + 16);
+        if (!na) return ZD_ERR_OOM;
+        ZD_CUDA(cudaMemcpyAsync(na, t->alive, sizeof(u32) * t->id_cap, cudaMemcpyDeviceToDevice, s));
+        k_fill_u32<<<grid_for(nc - t->id_cap, 256, 4096), 256, 0, s>>>(na, t->id_cap, nc, 0u);
+        for (int i = 0; i < t->nblocks; ++i)
+            if (t->blocks[i].p == t->alive) {
+                mem.put(t->blocks[i].p, t->blocks[i].bytes);
+                t->blocks[i] = Block{na, sizeof(u32) * (size_t)nc + 16};
+            }
+        t->alive = na;
+        t->id_cap = nc;
+    }
+    // the previous call's device errors must not be mistaken for this one's
+    int prior = zd_check(stream);
+    if (prior != ZD_OK) return prior;
+    int r = update_insert(view_of(t), t->keys, t->pts, t->n, d_pts, b, t->p.dim, t->B, t->p.shift,
+                          t->key_bits, (int32_t)t->next_id, t->keys2, t->pts2, t->alive, d_new_ids, mem);
+    if (r != ZD_OK) return r;
+    int st = zd_check(stream);
+    if (st != ZD_OK) {
+        // nothing was committed: the new ids are released again
+        k_fill_u32<<<grid_for(b, 256, 4096), 256, 0, s>>>(t->alive, t->next_id, t->next_id + b, 0u);
+        return st;
+    }
+    std::swap(t->keys, t->keys2);
+    std::swap(t->pts, t->pts2);
+    t->n += b;
+    t->next_id += b;
+    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, topo_of(t), mem));
+    return mem.failed ? ZD_ERR_OOM : ZD_OK;
+}
+
+extern "C" int zd_delete_batch(zd_tree *t, const int32_t *d_ids, int64_t b, void *stream)
+{
+    if (!t || b < 0 || (b > 0 && !d_ids)) return ZD_ERR_INVALID_ARG;
+    if (t->cloud_off || t->is_float) return ZD_ERR_UNIMPLEMENTED;
+    if (b == 0) return ZD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Mem mem = mem_of(t, s);
+    int prior = zd_check(stream);
+    if (prior != ZD_OK) return prior;
+    int result = ZD_OK;
+    ZD_TRY(update_delete_mark(t->alive, t->id_cap, d_ids, b, mem, &result));
+    if (result != ZD_OK) {
+        ZD_TRY(update_delete_unmark(t->alive, t->id_cap, d_ids, b, s));
+        ZD_CUDA(cudaStreamSynchronize(s));
+        return result;
+    }
+    if (b > t->n) return ZD_ERR_NOT_FOUND;
+    ZD_TRY(update_delete_compact(t->keys, t->pts, t->n, t->alive, d_ids, b, t->id_cap, t->keys2, t->pts2,
+                                 mem));
+    std::swap(t->keys, t->keys2);
+    std::swap(t->pts, t->pts2);
+    t->n -= b;
+    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, topo_of(t), mem));
+    int st = zd_check(stream);
+    if (st != ZD_OK) return st;
+    return mem.failed ? ZD_ERR_OOM : ZD_OK;
+}
+
+extern "C" int zd_knn_dist_backward(const float *d_q, const float *d_ref, const int32_t *d_idx,
+                                    int64_t batch, int64_t m, int64_t r, int dim, int k,
+                                    const float *d_gout, int gout_per_pair, float *d_gq,
+                                    float *d_gref, void *stream)
+{
+    if (batch < 0 || m < 0 || r < 0 || k < 1 || (dim != 2 && dim != 3)) return ZD_ERR_INVALID_ARG;
+    if (batch * m * k >= ((int64_t)1 << 31) - 2 || batch * r >= ((int64_t)1 << 31) - 2)
+        return ZD_ERR_INVALID_ARG;
+    if (!d_gout || (batch * m > 0 && (!d_q || !d_idx || !d_gq)) || (batch * r > 0 && (!d_ref || !d_gref)))
+        return ZD_ERR_INVALID_ARG;
+    if (!status_word()) return ZD_ERR_CUDA;
+    Mem mem;
+    mem.a = nullptr;
+    mem.s = (cudaStream_t)stream;
+    int rr = launch_backward(d_q, d_ref, d_idx, batch, m, r, dim, k, d_gout, gout_per_pair, d_gq, d_gref,
+                             mem);
+    if (rr == ZD_OK && mem.failed) rr = ZD_ERR_OOM;
+    return rr;
+}

@@ -1,0 +1,183 @@
+// common.cuh -- internal declarations shared by the libzd translation units.
+//
+// Device layout of a tree (all arrays owned by the tree, sized by capacity):
+//   keys[n]      uint64 Morton keys in sorted order (cloud id above the Morton
+//                bits for a batched forest)
+//   pts[n]       int4 (x, y, z, id) in sorted order; float trees keep the
+//                float bit patterns in x, y, z.  One 16-byte load per point.
+//   leaf_of[n]   index of the leaf holding each sorted position
+//   leaf_lo[]    leaf j holds sorted positions [leaf_lo[j], leaf_lo[j+1])
+//   internal node i (0 <= i < n_leaves - 1; node 0 is the root):
+//     ichild[i]  int2 (left, right): >= 0 internal node, < 0 leaf ~c
+//     iparent[i], ibit[i] (split bit), ibox[2i], ibox[2i+1] (lo, hi corners)
+//   leaf j: lparent[j], lbox[2j], lbox[2j+1]
+//   meta[0]      n_leaves (device-resident so that a build needs no host sync)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/zd.h"
+
+namespace zdk {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// ------------------------------------------------------------------ status
+// Device-wide status word: the first data-dependent error wins.
+__device__ __forceinline__ void set_status(u32 *status, int code)
+{
+    atomicCAS(status, 0u, (u32)code);
+}
+
+// Host: address of this device's status word (looked up once per device).
+u32 *status_word();
+
+// ----------------------------------------------------------------- memory
+struct Mem {
+    const zd_allocator *a;
+    cudaStream_t s;
+    bool failed = false;
+    void *get(size_t bytes);
+    void put(void *p, size_t bytes);
+};
+
+// A scratch block returned to the allocator when it goes out of scope.
+template <typename T>
+struct Scratch {
+    Mem *m = nullptr;
+    T *p = nullptr;
+    size_t bytes = 0;
+    Scratch() {}
+    Scratch(Mem &mem, size_t count) : m(&mem), bytes(count * sizeof(T) + 16)
+    {
+        p = (T *)mem.get(bytes);
+    }
+    ~Scratch()
+    {
+        if (p) m->put(p, bytes);
+    }
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+};
+
+// ------------------------------------------------------------- tree view
+struct TreeView {
+    int n;
+    int dim;
+    int coord_bits;
+    int cloud_bit;       // 64 for a single tree; dim*B for a batched forest
+    const u64 *keys;
+    const int4 *pts;
+    const int *leaf_of;
+    const int *leaf_lo;
+    const int *meta;
+    const int2 *ichild;
+    const int *iparent;
+    const int *ibit;
+    const int2 *irange;   // sorted-position range [x, y) of internal nodes
+    const int4 *ibox;
+    const int *lparent;
+    const int4 *lbox;
+    const int64_t *cloud_off; // batched: device offsets [n_clouds + 1], else nullptr
+};
+
+struct zd_tree_impl;
+
+// --------------------------------------------------------------- sorting
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 256;
+constexpr int MAX_PASSES = 8;
+
+// Encode integer points to Morton keys and (optionally) accumulate the digit
+// histograms of all passes (hist may be null).  With seg_off (device offsets
+// [n_seg + 1]) the segment (cloud) id of every row is placed at cloud_shift.
+int launch_encode_i32(const int32_t *pts, int64_t n, int dim, int coord_bits, const uint32_t *shift,
+                      const int64_t *seg_off, int64_t n_seg, int cloud_shift, u64 *keys, u32 *hist,
+                      int npasses, cudaStream_t s);
+
+// Float points: per-segment quantization frames (lo_x, lo_y, lo_z, scale),
+// frame: device double [n_seg * 4]; mm: device int scratch [n_seg * 6].
+int launch_float_frames(const float *pts, int64_t n, int dim, int coord_bits,
+                        const int64_t *seg_off, int64_t n_seg, int64_t max_seg, double *frame,
+                        int *mm, cudaStream_t s);
+int launch_encode_f32(const float *pts, int64_t n, int dim, int coord_bits, const double *frame,
+                      const int64_t *seg_off, int64_t n_seg, int cloud_shift, u64 *keys, u32 *hist,
+                      int npasses, cudaStream_t s);
+
+// Stable LSD radix sort of keys_in (read only) into keys_out / perm_out.
+// hist: device [MAX_PASSES * RADIX] digit histograms of keys_in (already
+// accumulated), or null to have the sort compute them.
+int radix_sort(const u64 *keys_in, int64_t n, int key_bits, u64 *keys_out, int32_t *perm_out,
+               u32 *hist, Mem &mem);
+
+// ------------------------------------------------------------------ build
+// Gather sorted points: pts_out[i] = (coords of row perm[i], id), with
+// id = base_id + perm[i], or perm[i] - cloud_off[key >> cloud_bit] when
+// cloud_off is given.  Float points travel as their bit patterns.
+int launch_gather(const void *pts_in, int dim, int64_t n, const int32_t *perm,
+                  const u64 *sorted_keys, int cloud_bit, const int64_t *cloud_off, int32_t base_id,
+                  int4 *pts_out, cudaStream_t s);
+
+struct TopoBuffers {
+    int *leaf_of;
+    int *leaf_lo;
+    int *meta;
+    int2 *ichild;
+    int *iparent;
+    int *ibit;
+    int2 *irange;
+    int4 *ibox;
+    int *lparent;
+    int4 *lbox;
+    int *counter; // scratch [n] for the bottom-up box pass
+};
+
+// From sorted keys and points, build leaves, internal nodes and boxes.
+int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, int dim,
+                   int is_float, const TopoBuffers &b, Mem &mem);
+
+// -------------------------------------------------------------------- knn
+struct KnnArgs {
+    TreeView t;
+    int k;
+    int mode;              // ZD_SEARCH_*
+    int is_float;
+    // external queries, already in Morton order
+    const int4 *q;         // (x, y, z, row) in tree coordinates (float bits for float trees)
+    const u64 *qkey;       // Morton keys of the sorted queries (bit mode; cloud in batched root mode)
+    int64_t m;
+    int32_t *out_idx;
+    void *out_dist;
+};
+int launch_knn_i32(const KnnArgs &a, cudaStream_t s);
+int launch_knn_f32(const KnnArgs &a, cudaStream_t s);
+
+// --------------------------------------------------------------- backward
+int launch_backward(const float *q, const float *ref, const int32_t *idx, int64_t batch, int64_t m,
+                    int64_t r, int dim, int k, const float *gout, int gout_per, float *gq,
+                    float *gref, Mem &mem);
+
+} // namespace zdk
+
+// Host-side errors from the CUDA runtime become ZD_ERR_CUDA.
+#define ZD_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return ZD_ERR_CUDA;                                         \
+    } while (0)
+
+#define ZD_TRY(call)                                                                       \
+    do {                                                                                   \
+        int r_ = (call);                                                                   \
+        if (r_ != ZD_OK) return r_;                                                        \
+    } while (0)
+
+static inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}

@@ -1,0 +1,369 @@
+// knn_impl.cuh -- exact k-NN over the zd-tree (Algorithms 2 and 3).
+//
+// One thread per query; queries run in Morton order (Sec. 3.1: sorting the
+// queries makes neighbouring threads touch the same nodes, so a warp's loads
+// hit the same cache lines).  Each thread keeps its k best candidates in
+// registers, sorted by (squared distance, id) -- the total order that makes
+// ties have one answer -- and walks the tree with an explicit stack:
+//
+//   leaf-based / bit-based (Algorithm 3): scan the start leaf, then climb;
+//     at each ancestor, stop once no point outside the current node's box can
+//     be within the k-th distance, else search the sibling downwards.
+//   root-based (Algorithm 2): search down from the root.
+//
+// searchDown visits a node iff its box distance^2 <= the current k-th
+// distance^2 (non-strict, so an equal distance with a smaller id is never
+// pruned) and descends into the nearer child first.  A child's box distance
+// is computed once, when its parent is expanded, and kept on the stack; a
+// popped entry is re-tested against the k-th distance, which may have shrunk.
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+
+namespace zdk {
+
+constexpr int KNN_THREADS = 128;
+constexpr int KNN_STACK = 72; // depth <= 64 internal levels + slack
+
+template <bool FLOAT>
+struct Metric;
+
+// Integer coordinates: exact int64 squared distances.  Coordinate
+// differences fit in int32 because every coordinate lies in one window of
+// width 2^B, B <= 31.
+template <>
+struct Metric<false> {
+    typedef long long D;
+    struct Q {
+        int x, y, z;
+    };
+    __device__ static D inf() { return LLONG_MAX; }
+    __device__ static Q make(int4 p) { return Q{p.x, p.y, p.z}; }
+    template <int DIM>
+    __device__ static D dist(const Q &q, int4 p)
+    {
+        int dx = q.x - p.x, dy = q.y - p.y;
+        D s = (D)dx * dx + (D)dy * dy;
+        if (DIM == 3) {
+            int dz = q.z - p.z;
+            s += (D)dz * dz;
+        }
+        return s;
+    }
+    template <int DIM>
+    __device__ static D boxd(const Q &q, int4 lo, int4 hi)
+    {
+        int cx = max(max(lo.x - q.x, q.x - hi.x), 0);
+        int cy = max(max(lo.y - q.y, q.y - hi.y), 0);
+        D s = (D)cx * cx + (D)cy * cy;
+        if (DIM == 3) {
+            int cz = max(max(lo.z - q.z, q.z - hi.z), 0);
+            s += (D)cz * cz;
+        }
+        return s;
+    }
+    // No integer point outside [lo, hi] can be within thr: in every
+    // dimension the first coordinate outside the box (lo-1 or hi+1) is
+    // farther than sqrt(thr) from q.
+    template <int DIM>
+    __device__ static bool inside(const Q &q, int4 lo, int4 hi, D thr)
+    {
+        if (thr == inf()) return false;
+        long long m;
+        m = min((long long)q.x - lo.x + 1, (long long)hi.x + 1 - q.x);
+        if (m <= 0 || m * m <= thr) return false;
+        m = min((long long)q.y - lo.y + 1, (long long)hi.y + 1 - q.y);
+        if (m <= 0 || m * m <= thr) return false;
+        if (DIM == 3) {
+            m = min((long long)q.z - lo.z + 1, (long long)hi.z + 1 - q.z);
+            if (m <= 0 || m * m <= thr) return false;
+        }
+        return true;
+    }
+};
+
+// Float coordinates: the ranking value is an fp64 squared distance evaluated
+// as ((dx*dx + dy*dy) + dz*dz), dx = (double)q.x - (double)p.x, each
+// operation rounded to nearest with no contraction.
+template <>
+struct Metric<true> {
+    typedef double D;
+    struct Q {
+        double x, y, z;
+    };
+    __device__ static D inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    __device__ static Q make(int4 p)
+    {
+        return Q{(double)__int_as_float(p.x), (double)__int_as_float(p.y), (double)__int_as_float(p.z)};
+    }
+    template <int DIM>
+    __device__ static D dist(const Q &q, int4 p)
+    {
+        double dx = __dsub_rn(q.x, (double)__int_as_float(p.x));
+        double dy = __dsub_rn(q.y, (double)__int_as_float(p.y));
+        double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        if (DIM == 3) {
+            double dz = __dsub_rn(q.z, (double)__int_as_float(p.z));
+            s = __dadd_rn(s, __dmul_rn(dz, dz));
+        }
+        return s;
+    }
+    __device__ static double gap(double q, float lo, float hi)
+    {
+        double l = (double)lo, h = (double)hi;
+        if (q < l) return __dsub_rn(l, q);
+        if (q > h) return __dsub_rn(q, h);
+        return 0.0;
+    }
+    template <int DIM>
+    __device__ static D boxd(const Q &q, int4 lo, int4 hi)
+    {
+        double cx = gap(q.x, __int_as_float(lo.x), __int_as_float(hi.x));
+        double cy = gap(q.y, __int_as_float(lo.y), __int_as_float(hi.y));
+        double s = __dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy));
+        if (DIM == 3) {
+            double cz = gap(q.z, __int_as_float(lo.z), __int_as_float(hi.z));
+            s = __dadd_rn(s, __dmul_rn(cz, cz));
+        }
+        return s;
+    }
+    // A point outside the box in dimension j differs from q by more than the
+    // gap m_j to that face; rounding is monotone, so its ranking value is at
+    // least fl(m_j^2).  Stop iff fl(m_j^2) > thr in every dimension.
+    __device__ static bool side_ok(double q, float lo, float hi, double thr)
+    {
+        double a = __dsub_rn(q, (double)lo), b = __dsub_rn((double)hi, q);
+        double m = a < b ? a : b;
+        return m >= 0.0 && __dmul_rn(m, m) > thr;
+    }
+    template <int DIM>
+    __device__ static bool inside(const Q &q, int4 lo, int4 hi, D thr)
+    {
+        if (!(thr < inf())) return false;
+        if (!side_ok(q.x, __int_as_float(lo.x), __int_as_float(hi.x), thr)) return false;
+        if (!side_ok(q.y, __int_as_float(lo.y), __int_as_float(hi.y), thr)) return false;
+        if (DIM == 3 && !side_ok(q.z, __int_as_float(lo.z), __int_as_float(hi.z), thr)) return false;
+        return true;
+    }
+};
+
+// Insert (d, id) into the sorted k-best list (the caller checked that it
+// beats the current k-th entry).  Fully unrolled, so the list stays in
+// registers.
+template <int K, typename D>
+__device__ __forceinline__ void kb_insert(D (&bd)[K], int (&bi)[K], D d, int id)
+{
+    bool placed = false;
+#pragma unroll
+    for (int j = K - 1; j > 0; --j) {
+        const bool lt = d < bd[j - 1] || (d == bd[j - 1] && id < bi[j - 1]);
+        if (!placed) {
+            bd[j] = lt ? bd[j - 1] : d;
+            bi[j] = lt ? bi[j - 1] : id;
+        }
+        placed = placed || !lt;
+    }
+    if (!placed) {
+        bd[0] = d;
+        bi[0] = id;
+    }
+}
+
+template <int DIM, int K, bool FLOAT>
+__device__ __forceinline__ void scan_leaf(const TreeView &t, int leaf, int self,
+                                          const typename Metric<FLOAT>::Q &q,
+                                          typename Metric<FLOAT>::D (&bd)[K], int (&bi)[K])
+{
+    typedef Metric<FLOAT> M;
+    const int lo = __ldg(t.leaf_lo + leaf), hi = __ldg(t.leaf_lo + leaf + 1);
+    for (int p = lo; p < hi; ++p) {
+        if (p == self) continue; // all-points mode: the query itself (by position = by id)
+        const int4 c = __ldg(t.pts + p);
+        const typename M::D d = M::template dist<DIM>(q, c);
+        if (d < bd[K - 1] || (d == bd[K - 1] && c.w < bi[K - 1])) kb_insert<K>(bd, bi, d, c.w);
+    }
+}
+
+__device__ __forceinline__ void node_box(const TreeView &t, int v, int4 &lo, int4 &hi)
+{
+    const int4 *b = v < 0 ? t.lbox + 2 * (~v) : t.ibox + 2 * v;
+    lo = __ldg(b);
+    hi = __ldg(b + 1);
+}
+
+// searchDown (Algorithm 2) from node v whose box distance is dv.
+template <int DIM, int K, bool FLOAT>
+__device__ __forceinline__ void search_down(const TreeView &t, int v, typename Metric<FLOAT>::D dv,
+                                            int self, const typename Metric<FLOAT>::Q &q,
+                                            typename Metric<FLOAT>::D (&bd)[K], int (&bi)[K],
+                                            u32 *status)
+{
+    typedef Metric<FLOAT> M;
+    typedef typename M::D D;
+    int sn[KNN_STACK];
+    D sd[KNN_STACK];
+    int sp = 0;
+    sn[sp] = v;
+    sd[sp] = dv;
+    ++sp;
+    while (sp > 0) {
+        --sp;
+        const int u = sn[sp];
+        if (sd[sp] > bd[K - 1]) continue; // pruned by the (possibly shrunk) k-th distance
+        if (u < 0) {
+            scan_leaf<DIM, K, FLOAT>(t, ~u, self, q, bd, bi);
+            continue;
+        }
+        const int2 ch = __ldg(t.ichild + u);
+        int4 al, ah, bl, bh;
+        node_box(t, ch.x, al, ah);
+        node_box(t, ch.y, bl, bh);
+        const D da = M::template boxd<DIM>(q, al, ah);
+        const D db = M::template boxd<DIM>(q, bl, bh);
+        const D thr = bd[K - 1];
+        // push the farther child first so the nearer one is searched first
+        const int nf = da <= db ? ch.y : ch.x, nn = da <= db ? ch.x : ch.y;
+        const D df = da <= db ? db : da, dn = da <= db ? da : db;
+        if (sp + 2 > KNN_STACK) {
+            set_status(status, ZD_ERR_CUDA);
+            return;
+        }
+        if (df <= thr) {
+            sn[sp] = nf;
+            sd[sp] = df;
+            ++sp;
+        }
+        if (dn <= thr) {
+            sn[sp] = nn;
+            sd[sp] = dn;
+            ++sp;
+        }
+    }
+}
+
+template <int DIM, int K, bool FLOAT>
+__global__ void __launch_bounds__(KNN_THREADS) k_knn(KnnArgs a, u32 *status)
+{
+    typedef Metric<FLOAT> M;
+    typedef typename M::D D;
+    const TreeView &t = a.t;
+    const int64_t qi = (int64_t)blockIdx.x * KNN_THREADS + threadIdx.x;
+    if (qi >= a.m) return;
+
+    D bd[K];
+    int bi[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        bd[j] = M::inf();
+        bi[j] = INT_MAX;
+    }
+    const int nl = __ldg(t.meta);
+    const int root = nl > 1 ? 0 : ~0;
+    int4 qp;
+    int self = -1;
+    int64_t row;
+    if (a.mode == ZD_SEARCH_LEAF) {
+        qp = __ldg(t.pts + qi);
+        self = (int)qi;
+        row = qp.w;
+        if (t.cloud_off) row += __ldg(t.cloud_off + (__ldg(t.keys + qi) >> t.cloud_bit));
+    } else {
+        qp = __ldg(a.q + qi);
+        row = qp.w;
+    }
+    const typename M::Q q = M::make(qp);
+
+    if (t.n > 0) {
+        if (a.mode == ZD_SEARCH_ROOT) {
+            int v = root;
+            bool ok = true;
+            if (t.cloud_off) {
+                // descend to the root of the query's own cloud
+                const u64 cloud = __ldg(a.qkey + qi) >> t.cloud_bit;
+                while (v >= 0 && __ldg(t.ibit + v) >= t.cloud_bit) {
+                    const int2 ch = __ldg(t.ichild + v);
+                    v = ((cloud >> (__ldg(t.ibit + v) - t.cloud_bit)) & 1) ? ch.y : ch.x;
+                }
+                const int first = v >= 0 ? __ldg(t.irange + v).x : __ldg(t.leaf_lo + ~v);
+                const int last = v >= 0 ? __ldg(t.irange + v).y : __ldg(t.leaf_lo + ~v + 1);
+                ok = last > first && (__ldg(t.keys + first) >> t.cloud_bit) == cloud;
+            }
+            if (ok) {
+                int4 lo, hi;
+                node_box(t, v, lo, hi);
+                search_down<DIM, K, FLOAT>(t, v, M::template boxd<DIM>(q, lo, hi), -1, q, bd, bi, status);
+            }
+        } else {
+            int leaf;
+            if (a.mode == ZD_SEARCH_LEAF) {
+                leaf = __ldg(t.leaf_of + qi);
+            } else {
+                // bit-based: descend by the query's Morton bits (Sec. 2)
+                const u64 key = __ldg(a.qkey + qi);
+                int v = root;
+                while (v >= 0) {
+                    const int2 ch = __ldg(t.ichild + v);
+                    v = ((key >> __ldg(t.ibit + v)) & 1) ? ch.y : ch.x;
+                }
+                leaf = ~v;
+            }
+            // searchUp (Algorithm 3)
+            scan_leaf<DIM, K, FLOAT>(t, leaf, self, q, bd, bi);
+            int node = ~leaf;
+            int par = __ldg(t.lparent + leaf);
+            while (par >= 0 && __ldg(t.ibit + par) < t.cloud_bit) {
+                int4 lo, hi;
+                node_box(t, node, lo, hi);
+                if (M::template inside<DIM>(q, lo, hi, bd[K - 1])) break;
+                const int2 ch = __ldg(t.ichild + par);
+                const int sib = ch.x == node ? ch.y : ch.x;
+                node_box(t, sib, lo, hi);
+                const D ds = M::template boxd<DIM>(q, lo, hi);
+                if (ds <= bd[K - 1]) search_down<DIM, K, FLOAT>(t, sib, ds, self, q, bd, bi, status);
+                node = par;
+                par = __ldg(t.iparent + par);
+            }
+        }
+    }
+
+    const int k = a.k;
+    int32_t *oi = a.out_idx + row * k;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if (j < k) oi[j] = bd[j] < M::inf() ? bi[j] : -1;
+    if (a.out_dist) {
+        if (FLOAT) {
+            float *od = (float *)a.out_dist + row * k;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (j < k) od[j] = bd[j] < M::inf() ? (float)sqrt((double)bd[j]) : __int_as_float(0x7f800000);
+        } else {
+            long long *od = (long long *)a.out_dist + row * k;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (j < k) od[j] = (long long)bd[j];
+        }
+    }
+}
+
+template <int DIM, bool FLOAT>
+int launch_knn_dim(const KnnArgs &a, cudaStream_t s)
+{
+    const unsigned g = (unsigned)((a.m + KNN_THREADS - 1) / KNN_THREADS);
+    if (a.m <= 0) return ZD_OK;
+    u32 *st = status_word();
+    if (a.k <= 1) k_knn<DIM, 1, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 2) k_knn<DIM, 2, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 4) k_knn<DIM, 4, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 5) k_knn<DIM, 5, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 8) k_knn<DIM, 8, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 10) k_knn<DIM, 10, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 16) k_knn<DIM, 16, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else k_knn<DIM, 32, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+} // namespace zdk

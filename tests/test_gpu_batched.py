@@ -1,0 +1,65 @@
+"""GPU batched forest: every cloud's subtree is that cloud's own canonical
+tree, and all-points k-NN never leaves a cloud (ids are cloud-local)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def zd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2111_04182_gb300 import zd as z
+
+    return z
+
+
+def test_batched_all_points_per_cloud(zd, oracle):
+    from paper_2111_04182_gb300 import datagen
+    w = datagen.workload_batched(n_clouds=40, seed=3, size_range=(1, 9000))
+    # drop cloud 4's points: an empty cloud in the middle of the forest
+    off2 = np.zeros(41, np.int64)
+    chunks = []
+    for c in range(40):
+        sz = 0 if c == 4 else int(w["offsets"][c + 1] - w["offsets"][c])
+        chunks.append(w["pts"][w["offsets"][c]:w["offsets"][c] + sz])
+        off2[c + 1] = off2[c] + sz
+    pts = np.concatenate(chunks)
+    t = zd.zd_build_batched(torch.from_numpy(pts).to(DEV), off2, 16, 16)
+    idx, d2 = zd.zd_knn_batched(t, 16)
+    assert zd.zd_check() == 0
+    idx, d2 = idx.cpu().numpy(), d2.cpu().numpy()
+    for c in range(40):
+        a, z = off2[c], off2[c + 1]
+        if z == a:
+            continue
+        cloud = pts[a:z]
+        ot = oracle.OracleTree(cloud, 16, 16)
+        oi, od = ot.knn(16)
+        assert np.array_equal(idx[a:z], oi), c
+        assert np.array_equal(d2[a:z], od), c
+    t.free()
+
+
+def test_batched_external_float_queries(zd, oracle):
+    from paper_2111_04182_gb300 import datagen
+    rng = np.random.default_rng(12)
+    P = 5
+    A, B = zip(*[datagen.warped_pair(rng, 700 + 100 * p, 1500 + 50 * p) for p in range(P)])
+    offA = np.concatenate([[0], np.cumsum([len(a) for a in A])])
+    offB = np.concatenate([[0], np.cumsum([len(b) for b in B])])
+    t = zd.zd_build_batched(torch.from_numpy(np.concatenate(B)).to(DEV), offB, 8, 21)
+    idx, dist = zd.zd_knn_batched(t, 8, queries=torch.from_numpy(np.concatenate(A)).to(DEV),
+                                  query_offsets=offA)
+    assert zd.zd_check() == 0
+    idx = idx.cpu().numpy()
+    for p in range(P):
+        bi, bd = oracle.knn_brute(B[p], 8, queries=A[p])
+        assert np.array_equal(idx[offA[p]:offA[p + 1]], bi), p
+    t.free()

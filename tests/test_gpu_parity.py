@@ -1,0 +1,220 @@
+"""GPU parity: every step of the path through the C ABI against the oracle.
+
+Integer work is compared bit-exactly (keys, sorted order, tree shape and
+boxes, neighbour ids and squared distances).  Sizes span several tiles of
+every kernel (4096-key sort tiles, 1024-boundary split tiles, 128-query k-NN
+blocks) plus a ragged tail.
+"""
+import numpy as np
+import pytest
+
+from tests._checks import brute_knn, check_tree
+from tests._gpu import canonical, nodes_of
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def zd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2111_04182_gb300 import zd as z
+
+    assert z.zd_check() == 0
+    return z
+
+
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+# --------------------------------------------------------------- encode
+@pytest.mark.parametrize("dim,bits,shift", [(3, 21, None), (2, 20, None), (2, 31, [5, 7]), (3, 18, [3, 1000, 77])])
+def test_encode_matches_oracle(zd, oracle, dim, bits, shift):
+    rng = np.random.default_rng(dim * 100 + bits)
+    hi = 2 ** bits - (max(shift) if shift else 0)
+    for n in (0, 1, 31, 4097, 100_003):
+        pts = rng.integers(0, hi, size=(n, dim)).astype(np.int32)
+        keys = zd.zd_morton_encode(_t(pts), bits, shift).cpu().numpy().view(np.uint64)
+        assert np.array_equal(keys, oracle.morton_keys(pts, bits, shift))
+    assert zd.zd_check() == 0
+
+
+def test_encode_range_error(zd):
+    pts = np.array([[0, 0, 0], [2 ** 21, 0, 0]], np.int32)
+    zd.zd_morton_encode(_t(pts), 21)
+    assert zd.zd_check() == zd.ZD_ERR_RANGE
+    assert zd.zd_check() == 0  # cleared
+
+
+# ----------------------------------------------------------------- sort
+@pytest.mark.parametrize("n", [0, 1, 2, 4095, 4096, 4097, 3 * 4096 + 17, 250_001])
+@pytest.mark.parametrize("kind", ["random64", "ties", "equal", "morton"])
+def test_sort_matches_lexsort(zd, oracle, n, kind):
+    rng = np.random.default_rng(n + len(kind))
+    if kind == "random64":
+        keys = rng.integers(0, 2 ** 63, size=n, dtype=np.int64).view(np.uint64) ^ (
+            rng.integers(0, 2, size=n).astype(np.uint64) << np.uint64(63))
+        bits = 64
+    elif kind == "ties":
+        keys = rng.integers(0, 37, size=n).astype(np.uint64) << np.uint64(20)
+        bits = 26
+    elif kind == "equal":
+        keys = np.full(n, 12345, np.uint64)
+        bits = 20
+    else:
+        keys = oracle.morton_keys(rng.integers(0, 2 ** 21, size=(n, 3)).astype(np.int32), 21)
+        bits = 63
+    sk, perm = zd.zd_morton_sort(_t(keys.view(np.int64)), bits)
+    assert zd.zd_check() == 0
+    want = np.lexsort((np.arange(n), keys))
+    assert np.array_equal(perm.cpu().numpy(), want)
+    assert np.array_equal(sk.cpu().numpy().view(np.uint64), keys[want])
+
+
+# ----------------------------------------------------------------- tree
+def _compare_tree(zd, oracle, pts, L, bits, shift=None):
+    t = zd.zd_build(_t(pts), L, bits, shift)
+    assert zd.zd_check() == 0
+    g = nodes_of(t.export())
+    ot = oracle.OracleTree(pts, L, bits, shift)
+    o = ot.canonical_dump()
+    assert np.array_equal(g["ids"], o["ids"]), "sorted order"
+    assert np.array_equal(g["keys"], o["keys"]), "sorted keys"
+    c = canonical(g)
+    for f in ("lo", "hi", "bit"):
+        assert np.array_equal(c[f], o[f]), "tree shape: " + f
+    nonempty = c["hi"] > c["lo"]
+    assert np.array_equal(c["box_lo"][nonempty], o["box_lo"][nonempty]), "boxes"
+    assert np.array_equal(c["box_hi"][nonempty], o["box_hi"][nonempty]), "boxes"
+    coords = pts[g["ids"].astype(np.int64)]
+    check_tree(g["keys"], g["lo"], g["hi"], g["bit"], L, coords=coords, box_lo=g["box_lo"],
+               box_hi=g["box_hi"], left=g["left"], right=g["right"], parent=g["parent"], root=g["root"])
+    return t
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("L", [1, 4, 16, 33])
+def test_build_matches_oracle(zd, oracle, dim, L):
+    rng = np.random.default_rng(dim * 10 + L)
+    bits = 21 if dim == 3 else 20
+    for n in (1, 2, 17, 5000, 70_001):
+        pts = rng.integers(0, 2 ** (bits - 1), size=(n, dim)).astype(np.int32)
+        _compare_tree(zd, oracle, pts, L, bits).free()
+    c = rng.integers(0, 2 ** 19, size=(8, dim))
+    pts = np.clip(c[rng.integers(0, 8, 30000)] + rng.integers(-4, 5, size=(30000, dim)), 0, 2 ** 19).astype(np.int32)
+    _compare_tree(zd, oracle, pts, L, bits).free()  # clustered, many duplicates
+
+
+def test_build_degenerate(zd, oracle):
+    _compare_tree(zd, oracle, np.full((5000, 3), 7, np.int32), 16, 21).free()  # one oversize leaf
+    _compare_tree(zd, oracle, np.random.default_rng(0).integers(0, 100, (40, 2)).astype(np.int32), 64, 20).free()
+    x = np.arange(3000, dtype=np.int32)
+    _compare_tree(zd, oracle, np.stack([x, x * 0 + 5, x * 0 + 9], 1), 8, 21).free()  # collinear
+    _compare_tree(zd, oracle, np.zeros((0, 3), np.int32), 16, 21).free()  # empty
+    g = np.stack(np.meshgrid(*[np.arange(16)] * 3, indexing="ij"), -1).reshape(-1, 3).astype(np.int32)
+    _compare_tree(zd, oracle, g, 8, 4).free()  # full lattice: perfect tree
+    _compare_tree(zd, oracle, g, 8, 21, shift=[1000, 2000, 3000]).free()
+
+
+# ------------------------------------------------------------------ kNN
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("k", [1, 3, 5, 10, 16, 32])
+def test_knn_all_points(zd, oracle, dim, k):
+    rng = np.random.default_rng(dim * 1000 + k)
+    bits = 21 if dim == 3 else 20
+    c = rng.integers(0, 2 ** 19, size=(12, dim))
+    pts = np.clip(c[rng.integers(0, 12, 40_000)] + rng.normal(0, 2000, (40_000, dim)), 0, 2 ** 19).astype(np.int32)
+    pts[:300] = pts[300:600]  # duplicates: ties at d^2 = 0
+    t = zd.zd_build(_t(pts), 16, bits)
+    idx, d2 = t.knn(k)
+    assert zd.zd_check() == 0
+    oi, od = oracle.OracleTree(pts, 16, bits).knn(k)
+    assert np.array_equal(d2.cpu().numpy(), od)
+    assert np.array_equal(idx.cpu().numpy(), oi)
+    t.free()
+
+
+def test_knn_small_and_padding(zd, oracle):
+    for n, k, L in ((1, 4, 16), (2, 4, 1), (7, 10, 2), (33, 32, 4), (300, 5, 1)):
+        pts = np.random.default_rng(n).integers(0, 1000, size=(n, 3)).astype(np.int32)
+        t = zd.zd_build(_t(pts), L, 21)
+        idx, d2 = t.knn(k)
+        bi, bd = brute_knn(pts, k)
+        assert np.array_equal(idx.cpu().numpy(), bi) and np.array_equal(d2.cpu().numpy(), bd)
+        t.free()
+    assert zd.zd_check() == 0
+
+
+def test_knn_lattice_ties(zd, oracle):
+    g = (np.stack(np.meshgrid(*[np.arange(20)] * 3, indexing="ij"), -1).reshape(-1, 3) * 3).astype(np.int32)
+    t = zd.zd_build(_t(g), 16, 21)
+    idx, d2 = t.knn(10)
+    oi, od = oracle.OracleTree(g, 16, 21).knn(10)
+    assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+    t.free()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_knn_external_queries(zd, oracle, mode, dim):
+    rng = np.random.default_rng(mode * 7 + dim)
+    bits = 21 if dim == 3 else 20
+    pts = rng.integers(0, 2 ** 20, size=(60_000, dim)).astype(np.int32)
+    q = rng.integers(0, 2 ** 20, size=(9_001, dim)).astype(np.int32)
+    q[:50] = pts[:50]
+    t = zd.zd_build(_t(pts), 16, bits)
+    idx, d2 = t.knn(5, queries=_t(q), mode=mode)
+    assert zd.zd_check() == 0
+    oi, od = oracle.knn_brute(pts, 5, queries=q)
+    assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+    t.free()
+
+
+def test_knn_2d_uniform_workload(zd, oracle):
+    """The 2D workload at its full size: n = 100,000, L = 16, k = 10."""
+    from paper_2111_04182_gb300 import datagen
+    w = datagen.workload_2d_uniform()
+    t = zd.zd_build(_t(w["pts"]), w["leaf_size"], w["coord_bits"])
+    _ = _compare_tree
+    g = nodes_of(t.export())
+    ot = oracle.OracleTree(w["pts"], w["leaf_size"], w["coord_bits"])
+    o = ot.canonical_dump()
+    c = canonical(g)
+    assert np.array_equal(c["lo"], o["lo"]) and np.array_equal(c["bit"], o["bit"])
+    idx, d2 = t.knn(w["k"])
+    oi, od = ot.knn(w["k"])
+    assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+    t.free()
+    assert zd.zd_check() == 0
+
+
+# --------------------------------------------------------------- float
+def test_float_knn_fp64_ranking(zd, oracle):
+    from paper_2111_04182_gb300 import datagen
+    rng = np.random.default_rng(77)
+    a, b = datagen.warped_pair(rng, 6000, 12000)
+    t = zd.zd_build(_t(b), 16, 21)
+    e = nodes_of(t.export())
+    lo, scale = oracle.quantization_of(b, 21)
+    ot = oracle.OracleTree(b, 16, 21, qlo=lo, qscale=scale)
+    o = ot.canonical_dump()
+    assert np.array_equal(e["keys"], o["keys"]), "float quantization / keys"
+    assert np.array_equal(canonical(e)["bit"], o["bit"])
+    for mode in (1, 2):
+        idx, dist = t.knn(8, queries=_t(a), mode=mode)
+        bi, bd = oracle.knn_brute(b, 8, queries=a)
+        assert np.array_equal(idx.cpu().numpy(), bi)
+        assert np.allclose(dist.cpu().numpy(), np.sqrt(bd), rtol=1e-6, atol=0)
+    idx, dist = t.knn(6)
+    bi, bd = oracle.knn_brute(b, 6)
+    assert np.array_equal(idx.cpu().numpy(), bi)
+    t.free()
+    assert zd.zd_check() == 0
