@@ -63,6 +63,14 @@ enum { ZD_COORD_I32 = 0, ZD_COORD_F32 = 1 };
  * the root). */
 enum { ZD_SEARCH_LEAF = 0, ZD_SEARCH_BIT = 1, ZD_SEARCH_ROOT = 2 };
 
+/* Optional thread mapping of a search, OR-ed into the mode of zd_knn /
+ * zd_knn_batched (default: the library's choice).  ZD_KNN_THREAD_PER_QUERY:
+ * one thread runs one query's traversal.  ZD_KNN_WARP_GROUP (leaf-based mode,
+ * integer trees): one warp runs one shared traversal for 32 consecutive
+ * points in Morton order, each lane keeping its own k best.  Both return the
+ * same exact neighbours. */
+enum { ZD_KNN_THREAD_PER_QUERY = 0x100, ZD_KNN_WARP_GROUP = 0x200 };
+
 /* Largest k of one search (neighbour lists are register-resident). */
 #define ZD_MAX_K 32
 
@@ -223,9 +231,10 @@ int zd_build_batched(const zd_params *p, const zd_allocator *alloc, const void *
  * d_queries NULL: all points of every cloud (row = global row of the point in
  * the build input, ids local); else external queries [m, dim] with
  * d_query_offsets [n_clouds + 1] (device) assigning rows to clouds, searched
- * root-based within their cloud.  Outputs as zd_knn. */
+ * root-based within their cloud.  mode_flags: 0 or one ZD_KNN_* mapping flag.
+ * Outputs as zd_knn. */
 int zd_knn_batched(const zd_tree *t, const void *d_queries, const int64_t *d_query_offsets,
-                   int64_t m, int k, int32_t *d_idx, void *d_dist, void *stream);
+                   int64_t m, int k, int mode_flags, int32_t *d_idx, void *d_dist, void *stream);
 
 #ifdef __cplusplus
 }

@@ -75,10 +75,14 @@ struct zd_tree {
     int *lparent;
     int4 *lbox;
     int *counter;
+    float4 *fpts, *fibox, *flbox; // integer trees with B <= 24: exact float copies
     double *frame;      // float trees: [n_clouds * 4]
     int64_t *cloud_off; // forests: [n_clouds + 1]
     u32 *alive;         // dynamic trees: per id, 1 = live, 2 = marked for delete
     int64_t id_cap;
+    int64_t max_cloud;  // largest cloud (forests): bounds the local ids
+    int *group_start;   // forests: first sorted position of every 32-point group
+    int64_t n_groups;
     Block blocks[32];
     int nblocks;
 };
@@ -129,6 +133,9 @@ static TreeView view_of(const zd_tree *t)
     v.lparent = t->lparent;
     v.lbox = t->lbox;
     v.cloud_off = t->cloud_off;
+    v.fpts = t->fpts;
+    v.fibox = t->fibox;
+    v.flbox = t->flbox;
     return v;
 }
 
@@ -146,6 +153,9 @@ static TopoBuffers topo_of(zd_tree *t)
     b.lparent = t->lparent;
     b.lbox = t->lbox;
     b.counter = t->counter;
+    b.fpts = t->fpts;
+    b.fibox = t->fibox;
+    b.flbox = t->flbox;
     return b;
 }
 
@@ -181,6 +191,9 @@ static int tree_arrays(zd_tree *t, Mem &m, bool dynamic)
               tree_alloc(t, m, &t->lparent, cap + 1) && tree_alloc(t, m, &t->lbox, 2 * cap + 2) &&
               tree_alloc(t, m, &t->counter, cap);
     if (ok && t->is_float) ok = tree_alloc(t, m, &t->frame, 4 * (size_t)t->n_clouds);
+    if (ok && !t->is_float && t->B <= 24)
+        ok = tree_alloc(t, m, &t->fpts, cap) && tree_alloc(t, m, &t->fibox, 2 * cap) &&
+             tree_alloc(t, m, &t->flbox, 2 * cap + 2);
     if (ok && dynamic) {
         ok = tree_alloc(t, m, &t->keys2, cap) && tree_alloc(t, m, &t->pts2, cap);
     }
@@ -226,7 +239,7 @@ static int build_core(zd_tree *t, const void *d_pts, const int64_t *seg_off, int
     }
     ZD_TRY(radix_sort(raw.p, n, t->key_bits, t->keys, perm.p, hist.p, m));
     ZD_TRY(launch_gather(d_pts, dim, n, perm.p, t->keys, t->cloud_bit, t->cloud_off, 0, t->pts, s));
-    ZD_TRY(build_topology(t->keys, t->pts, n, t->p.leaf_size, dim, t->is_float, topo_of(t), m));
+    ZD_TRY(build_topology(t->keys, t->pts, n, t->p.leaf_size, dim, t->is_float, t->cloud_bit, topo_of(t), m));
     return m.failed ? ZD_ERR_OOM : ZD_OK;
 }
 
@@ -375,6 +388,13 @@ int zd_build_batched(const zd_params *p, const zd_allocator *alloc, const void *
                                       cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         r = ZD_ERR_CUDA;
     if (r == ZD_OK) r = build_core(t, d_pts, t->cloud_off, n_clouds, max_seg, s);
+    // 32-point groups that never cross a cloud, for the warp-group search
+    t->max_cloud = max_seg;
+    t->n_groups = 0;
+    for (int64_t c = 0; c < n_clouds; ++c) t->n_groups += (h_offsets[c + 1] - h_offsets[c] + 31) / 32;
+    if (r == ZD_OK && !tree_alloc(t, m, &t->group_start, (size_t)std::max<int64_t>(t->n_groups, 1)))
+        r = ZD_ERR_OOM;
+    if (r == ZD_OK) r = launch_group_starts(t->cloud_off, n_clouds, t->n_groups, t->group_start, m);
     if (r != ZD_OK) {
         tree_release(t, s);
         free(t);
@@ -514,7 +534,10 @@ static int prepare_queries(const zd_tree *t, const void *d_q, int64_t m, const i
 static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m, int k, int mode,
                    int32_t *d_idx, void *d_dist, cudaStream_t s)
 {
+    const int variant = mode & (ZD_KNN_THREAD_PER_QUERY | ZD_KNN_WARP_GROUP);
+    mode &= 0xff;
     KnnArgs a;
+    memset(&a, 0, sizeof(a));
     a.t = view_of(t);
     a.k = k;
     a.mode = mode;
@@ -524,7 +547,22 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
     a.m = m;
     a.out_idx = d_idx;
     a.out_dist = d_dist;
-    return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s);
+    a.shift = make_uint3(t->p.shift[0], t->p.shift[1], t->p.shift[2]);
+    // warp groups: integer trees, all points or bit-based external queries
+    const bool group = !t->is_float && variant != ZD_KNN_THREAD_PER_QUERY &&
+                       (mode == ZD_SEARCH_LEAF || (mode == ZD_SEARCH_BIT && !t->cloud_off));
+    if (!group) return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s);
+    // packed keys: the ids need idb bits
+    a.idb = std::max(1, ceil_log2(t->cloud_off ? t->max_cloud : t->next_id));
+    const bool allpts = mode == ZD_SEARCH_LEAF;
+    a.group_start = allpts ? t->group_start : nullptr;
+    a.n_groups = allpts ? (t->cloud_off ? t->n_groups : (t->n + 31) / 32) : (m + 31) / 32;
+    Mem mem = mem_of(t, s);
+    Scratch<int> fix(mem, (size_t)(allpts ? t->n : m) + 1);
+    if (!fix.p) return ZD_ERR_OOM;
+    a.fix_count = fix.p;
+    a.fix_list = fix.p + 1;
+    return launch_knn_group_i32(a, s);
 }
 
 extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k, int mode,
@@ -534,10 +572,13 @@ extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k,
     if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
     if (t->cloud_off) return ZD_ERR_INVALID_ARG; // forests: zd_knn_batched
     cudaStream_t s = (cudaStream_t)stream;
-    if (mode == ZD_SEARCH_LEAF) {
+    const int flags = mode & ~0xff;
+    if (flags & ~(ZD_KNN_THREAD_PER_QUERY | ZD_KNN_WARP_GROUP)) return ZD_ERR_INVALID_ARG;
+    if ((mode & 0xff) == ZD_SEARCH_LEAF) {
         if (d_queries) return ZD_ERR_INVALID_ARG;
         return run_knn(t, nullptr, nullptr, t->n, k, mode, d_idx, d_dist, s);
     }
+    mode &= 0xff;
     if (mode != ZD_SEARCH_BIT && mode != ZD_SEARCH_ROOT) return ZD_ERR_INVALID_ARG;
     if (m < 0 || m >= ((int64_t)1 << 31) - 2 || (m > 0 && !d_queries)) return ZD_ERR_INVALID_ARG;
     if (m == 0) return ZD_OK;
@@ -551,13 +592,15 @@ extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k,
 }
 
 extern "C" int zd_knn_batched(const zd_tree *t, const void *d_queries, const int64_t *d_query_offsets,
-                              int64_t m, int k, int32_t *d_idx, void *d_dist, void *stream)
+                              int64_t m, int k, int mode_flags, int32_t *d_idx, void *d_dist, void *stream)
 {
     if (!t || !d_idx || k < 1) return ZD_ERR_INVALID_ARG;
     if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
     if (!t->cloud_off) return ZD_ERR_INVALID_ARG;
+    if (mode_flags & ~(ZD_KNN_THREAD_PER_QUERY | ZD_KNN_WARP_GROUP)) return ZD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!d_queries) return run_knn(t, nullptr, nullptr, t->n, k, ZD_SEARCH_LEAF, d_idx, d_dist, s);
+    if (!d_queries)
+        return run_knn(t, nullptr, nullptr, t->n, k, ZD_SEARCH_LEAF | mode_flags, d_idx, d_dist, s);
     if (!d_query_offsets || m < 0 || m >= ((int64_t)1 << 31) - 2) return ZD_ERR_INVALID_ARG;
     if (m == 0) return ZD_OK;
     Mem mem = mem_of(t, s);
@@ -621,7 +664,7 @@ extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t
     std::swap(t->pts, t->pts2);
     t->n += b;
     t->next_id += b;
-    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, topo_of(t), mem));
+    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), mem));
     return mem.failed ? ZD_ERR_OOM : ZD_OK;
 }
 
@@ -647,7 +690,7 @@ extern "C" int zd_delete_batch(zd_tree *t, const int32_t *d_ids, int64_t b, void
     std::swap(t->keys, t->keys2);
     std::swap(t->pts, t->pts2);
     t->n -= b;
-    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, topo_of(t), mem));
+    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), mem));
     int st = zd_check(stream);
     if (st != ZD_OK) return st;
     return mem.failed ? ZD_ERR_OOM : ZD_OK;

@@ -67,7 +67,8 @@ __device__ __forceinline__ int delta_of(u64 a, u64 b) { return a == b ? -1 : 63 
 // flag[i] = 1 iff boundary i (between sorted points i and i+1) separates two
 // leaves; block_count[b] = flags in block b's tile.
 __global__ void __launch_bounds__(FLAG_THREADS) k_split_flags(const u64 *__restrict__ keys, int64_t n,
-                                                              int L, unsigned char *__restrict__ flag,
+                                                              int L, int force_bit,
+                                                              unsigned char *__restrict__ flag,
                                                               int *__restrict__ block_count)
 {
     __shared__ int s_delta[FLAG_TILE + 2 * MAX_LEAF];
@@ -116,8 +117,9 @@ __global__ void __launch_bounds__(FLAG_THREADS) k_split_flags(const u64 *__restr
                 }
             }
             if (!found) ng = min(i + L, nb);
-            // the run bounded by pg and ng holds ng - pg points
-            f = (ng - pg > L) ? 1 : 0;
+            // the run bounded by pg and ng holds ng - pg points; a boundary
+            // between two clouds of a forest always separates leaves
+            f = (ng - pg > L || di >= force_bit) ? 1 : 0;
         }
         flag[i] = f;
         cnt += f;
@@ -304,6 +306,22 @@ struct BoxOps<true> {
     }
 };
 
+__device__ __forceinline__ float4 as_float4(int4 v)
+{
+    return make_float4((float)v.x, (float)v.y, (float)v.z, 0.f);
+}
+
+// Float copy of integer points (exact: coordinates lie in a window of width
+// <= 2^24), id bits kept in w.  The search filters candidates on it.
+__global__ void k_fpts(const int4 *__restrict__ pts, int64_t n, float4 *__restrict__ fpts)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int4 p = pts[i];
+        fpts[i] = make_float4((float)p.x, (float)p.y, (float)p.z, __int_as_float(p.w));
+    }
+}
+
 template <bool FLOAT>
 __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
                                                const int *__restrict__ leaf_lo,
@@ -311,7 +329,7 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
                                                const int2 *__restrict__ ichild,
                                                const int *__restrict__ iparent,
                                                const int *__restrict__ lparent, int4 *ibox,
-                                               int4 *lbox, int *counter)
+                                               int4 *lbox, int *counter, float4 *fibox, float4 *flbox)
 {
     typedef BoxOps<FLOAT> B;
     const int nl = meta[0];
@@ -327,6 +345,10 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
         }
         lbox[2 * j] = lo;
         lbox[2 * j + 1] = hi;
+        if (flbox) {
+            flbox[2 * j] = as_float4(lo);
+            flbox[2 * j + 1] = as_float4(hi);
+        }
         __threadfence();
         int p = lparent[j];
         while (p >= 0) {
@@ -336,16 +358,87 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
             const int4 *ba = ch.x < 0 ? lbox + 2 * (~ch.x) : ibox + 2 * ch.x;
             const int4 *bb = ch.y < 0 ? lbox + 2 * (~ch.y) : ibox + 2 * ch.y;
             int4 l0 = __ldcg(ba), h0 = __ldcg(ba + 1), l1 = __ldcg(bb), h1 = __ldcg(bb + 1);
-            ibox[2 * p] = B::mn(l0, l1);
-            ibox[2 * p + 1] = B::mx(h0, h1);
+            const int4 lo2 = B::mn(l0, l1), hi2 = B::mx(h0, h1);
+            ibox[2 * p] = lo2;
+            ibox[2 * p + 1] = hi2;
+            if (fibox) {
+                fibox[2 * p] = as_float4(lo2);
+                fibox[2 * p + 1] = as_float4(hi2);
+            }
             __threadfence();
             p = iparent[p];
         }
     }
 }
 
+// ---------------------------------------------------------- group starts
+// gpre[c] = number of 32-point groups in clouds before c (one block).
+__global__ void __launch_bounds__(1024) k_group_prefix(const int64_t *__restrict__ off, int64_t nc,
+                                                       int64_t *__restrict__ gpre)
+{
+    __shared__ int64_t s_w[32];
+    __shared__ int64_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nc; base += 1024) {
+        const int64_t c = base + threadIdx.x;
+        const int64_t v = c < nc ? (off[c + 1] - off[c] + 31) / 32 : 0;
+        int64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = s_w[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_w[lane] = w;
+        }
+        __syncthreads();
+        const int64_t excl = s_carry + (warp ? s_w[warp - 1] : 0) + x - v;
+        if (c < nc) gpre[c] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gpre[nc] = s_carry;
+}
+
+__global__ void k_group_starts(const int64_t *__restrict__ off, const int64_t *__restrict__ gpre, int64_t nc,
+                               int64_t ng, int *__restrict__ start)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = 0, z = nc - 1; // last cloud with gpre[c] <= g
+        while (a < z) {
+            int64_t mid = (a + z + 1) >> 1;
+            if (gpre[mid] <= g) a = mid;
+            else z = mid - 1;
+        }
+        start[g] = (int)(off[a] + 32 * (g - gpre[a]));
+    }
+}
+
+int launch_group_starts(const int64_t *cloud_off, int64_t n_clouds, int64_t n_groups, int *group_start,
+                        Mem &mem)
+{
+    if (n_groups <= 0) return ZD_OK;
+    Scratch<int64_t> gpre(mem, n_clouds + 1);
+    if (!gpre.p) return ZD_ERR_OOM;
+    k_group_prefix<<<1, 1024, 0, mem.s>>>(cloud_off, n_clouds, gpre.p);
+    k_group_starts<<<grid_for(n_groups, 256, 152 * 16), 256, 0, mem.s>>>(cloud_off, gpre.p, n_clouds, n_groups,
+                                                                        group_start);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
 int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, int dim,
-                   int is_float, const TopoBuffers &b, Mem &mem)
+                   int is_float, int force_bit, const TopoBuffers &b, Mem &mem)
 {
     (void)dim;
     cudaStream_t s = mem.s;
@@ -356,7 +449,8 @@ int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, i
     Scratch<int> bcount(mem, nblocks > 0 ? nblocks : 1);
     if (!flag.p || !bcount.p) return ZD_ERR_OOM;
     if (nblocks > 0) {
-        k_split_flags<<<(unsigned)nblocks, FLAG_THREADS, 0, s>>>(keys, n, leaf_size, flag.p, bcount.p);
+        k_split_flags<<<(unsigned)nblocks, FLAG_THREADS, 0, s>>>(keys, n, leaf_size, force_bit, flag.p,
+                                                                 bcount.p);
         ZD_CUDA(cudaGetLastError());
     }
     k_scan_counts<<<1, 1024, 0, s>>>(bcount.p, nblocks, n, b.meta, b.leaf_lo);
@@ -375,10 +469,14 @@ int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, i
     const int64_t max_leaves = n > 0 ? n : 1;
     if (is_float)
         k_boxes<true><<<grid_for(max_leaves, 256, 152 * 64), 256, 0, s>>>(
-            pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter);
+            pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter,
+            nullptr, nullptr);
     else
         k_boxes<false><<<grid_for(max_leaves, 256, 152 * 64), 256, 0, s>>>(
-            pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter);
+            pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter,
+            b.fibox, b.flbox);
+    if (!is_float && b.fpts && n > 0)
+        k_fpts<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(pts, n, b.fpts);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

@@ -81,6 +81,10 @@ struct TreeView {
     const int *lparent;
     const int4 *lbox;
     const int64_t *cloud_off; // batched: device offsets [n_clouds + 1], else nullptr
+    // exact float copies of integer points / boxes (coordinate window <= 2^24), or null
+    const float4 *fpts;
+    const float4 *fibox;
+    const float4 *flbox;
 };
 
 struct zd_tree_impl;
@@ -132,11 +136,21 @@ struct TopoBuffers {
     int *lparent;
     int4 *lbox;
     int *counter; // scratch [n] for the bottom-up box pass
+    // integer trees whose coordinates fit fp32 exactly: float copies, or null
+    float4 *fpts, *fibox, *flbox;
 };
 
 // From sorted keys and points, build leaves, internal nodes and boxes.
+// Boundaries whose highest differing key bit is >= force_bit (the cloud id
+// bits of a forest; 64 for one tree) always separate leaves, so every
+// cloud's subtree is that cloud's own canonical tree.
 int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, int dim,
-                   int is_float, const TopoBuffers &b, Mem &mem);
+                   int is_float, int force_bit, const TopoBuffers &b, Mem &mem);
+
+// Forests: group_start[g] = first sorted position of the g-th 32-point group,
+// groups laid out cloud by cloud so that none crosses a cloud boundary.
+int launch_group_starts(const int64_t *cloud_off, int64_t n_clouds, int64_t n_groups, int *group_start,
+                        Mem &mem);
 
 // -------------------------------------------------------------------- knn
 struct KnnArgs {
@@ -150,8 +164,19 @@ struct KnnArgs {
     int64_t m;
     int32_t *out_idx;
     void *out_dist;
+    uint3 shift;             // the tree's coordinate shift (Morton cells)
+    // warp-group mapping (integer coordinates)
+    int idb;                 // id bits of the packed (d^2, id) keys
+    const int *group_start;  // first sorted position of every group (forests), or null
+    int64_t n_groups;
+    int *fix_list;           // queries whose packed k-th distance saturated
+    int *fix_count;
+    // exact kernel restricted to listed sorted positions (fallback), or null
+    const int *sel;
+    const int *sel_count;
 };
 int launch_knn_i32(const KnnArgs &a, cudaStream_t s);
+int launch_knn_group_i32(const KnnArgs &a, cudaStream_t s); // + exact fallback
 int launch_knn_f32(const KnnArgs &a, cudaStream_t s);
 
 // --------------------------------------------------------------- backward

@@ -1,9 +1,21 @@
-// knn_i32.cu -- integer-coordinate instantiations of the k-NN search.
-#include "knn_impl.cuh"
+// knn_i32.cu -- integer-coordinate instantiations of the k-NN search: the
+// one-thread-per-query kernel and the warp-group all-points kernel.
+#include "knn_group.cuh"
 
 namespace zdk {
 int launch_knn_i32(const KnnArgs &a, cudaStream_t s)
 {
     return a.t.dim == 3 ? launch_knn_dim<3, false>(a, s) : launch_knn_dim<2, false>(a, s);
+}
+
+// Warp groups, then the exact kernel for the queries they handed back.
+int launch_knn_group_i32(const KnnArgs &a, cudaStream_t s)
+{
+    ZD_CUDA(cudaMemsetAsync(a.fix_count, 0, sizeof(int), s));
+    ZD_TRY(a.t.dim == 3 ? launch_knn_group_dim<3>(a, s) : launch_knn_group_dim<2>(a, s));
+    KnnArgs f = a;
+    f.sel = a.fix_list;
+    f.sel_count = a.fix_count;
+    return launch_knn_i32(f, s);
 }
 } // namespace zdk

@@ -193,6 +193,26 @@ __device__ __forceinline__ void node_box(const TreeView &t, int v, int4 &lo, int
     hi = __ldg(b + 1);
 }
 
+// Integer margin test against the Morton cell of a node whose parent splits
+// on key bit pbit: coordinate j's levels >= ceil((pbit - (d-1-j)) / d) are
+// the node's prefix, the rest is free.  True iff in every dimension the first
+// integer outside the cell is more than sqrt(thr) from the query.
+template <int DIM>
+__device__ __forceinline__ bool cell_inside(int4 qp, uint3 shift, int pbit, long long thr)
+{
+    if (thr == LLONG_MAX) return false;
+    const unsigned q3[3] = {(unsigned)qp.x + shift.x, (unsigned)qp.y + shift.y, (unsigned)qp.z + shift.z};
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        const int lj = max(0, (pbit - (DIM - 1 - j) + DIM - 1) / DIM);
+        const long long mask = (1ll << lj) - 1;
+        const long long off = (long long)(q3[j] & (unsigned)mask);
+        const long long m = min(off + 1, mask + 1 - off);
+        if (m * m <= thr) return false;
+    }
+    return true;
+}
+
 // searchDown (Algorithm 2) from node v whose box distance is dv.
 template <int DIM, int K, bool FLOAT>
 __device__ __forceinline__ void search_down(const TreeView &t, int v, typename Metric<FLOAT>::D dv,
@@ -244,13 +264,11 @@ __device__ __forceinline__ void search_down(const TreeView &t, int v, typename M
 }
 
 template <int DIM, int K, bool FLOAT>
-__global__ void __launch_bounds__(KNN_THREADS) k_knn(KnnArgs a, u32 *status)
+__device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u32 *status)
 {
     typedef Metric<FLOAT> M;
     typedef typename M::D D;
     const TreeView &t = a.t;
-    const int64_t qi = (int64_t)blockIdx.x * KNN_THREADS + threadIdx.x;
-    if (qi >= a.m) return;
 
     D bd[K];
     int bi[K];
@@ -315,8 +333,14 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(KnnArgs a, u32 *status)
             int par = __ldg(t.lparent + leaf);
             while (par >= 0 && __ldg(t.ibit + par) < t.cloud_bit) {
                 int4 lo, hi;
-                node_box(t, node, lo, hi);
-                if (M::template inside<DIM>(q, lo, hi, bd[K - 1])) break;
+                if (!FLOAT && a.mode == ZD_SEARCH_LEAF) {
+                    // the query lies in the node's Morton cell, which holds
+                    // every point the node can hold: stop on the cell
+                    if (cell_inside<DIM>(qp, a.shift, __ldg(t.ibit + par), (long long)bd[K - 1])) break;
+                } else {
+                    node_box(t, node, lo, hi);
+                    if (M::template inside<DIM>(q, lo, hi, bd[K - 1])) break;
+                }
                 const int2 ch = __ldg(t.ichild + par);
                 const int sib = ch.x == node ? ch.y : ch.x;
                 node_box(t, sib, lo, hi);
@@ -348,20 +372,42 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(KnnArgs a, u32 *status)
     }
 }
 
+template <int DIM, int K, bool FLOAT>
+__global__ void __launch_bounds__(KNN_THREADS) k_knn(KnnArgs a, u32 *status)
+{
+    const int64_t qi = (int64_t)blockIdx.x * KNN_THREADS + threadIdx.x;
+    if (qi < a.m) knn_query<DIM, K, FLOAT>(a, qi, status);
+}
+
+// The same search for the sorted positions listed in a.sel (all-points mode).
+template <int DIM, int K, bool FLOAT>
+__global__ void __launch_bounds__(KNN_THREADS) k_knn_sel(KnnArgs a, u32 *status)
+{
+    const int count = *a.sel_count;
+    for (int i = blockIdx.x * KNN_THREADS + threadIdx.x; i < count; i += gridDim.x * KNN_THREADS)
+        knn_query<DIM, K, FLOAT>(a, __ldg(a.sel + i), status);
+}
+
+template <int DIM, int K, bool FLOAT>
+void launch_knn_k(const KnnArgs &a, cudaStream_t s, u32 *st)
+{
+    if (a.sel) k_knn_sel<DIM, K, FLOAT><<<152 * 2, KNN_THREADS, 0, s>>>(a, st);
+    else k_knn<DIM, K, FLOAT><<<(unsigned)((a.m + KNN_THREADS - 1) / KNN_THREADS), KNN_THREADS, 0, s>>>(a, st);
+}
+
 template <int DIM, bool FLOAT>
 int launch_knn_dim(const KnnArgs &a, cudaStream_t s)
 {
-    const unsigned g = (unsigned)((a.m + KNN_THREADS - 1) / KNN_THREADS);
-    if (a.m <= 0) return ZD_OK;
+    if (a.m <= 0 && !a.sel) return ZD_OK;
     u32 *st = status_word();
-    if (a.k <= 1) k_knn<DIM, 1, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else if (a.k <= 2) k_knn<DIM, 2, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else if (a.k <= 4) k_knn<DIM, 4, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else if (a.k <= 5) k_knn<DIM, 5, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else if (a.k <= 8) k_knn<DIM, 8, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else if (a.k <= 10) k_knn<DIM, 10, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else if (a.k <= 16) k_knn<DIM, 16, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else k_knn<DIM, 32, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
+    if (a.k <= 1) launch_knn_k<DIM, 1, FLOAT>(a, s, st);
+    else if (a.k <= 2) launch_knn_k<DIM, 2, FLOAT>(a, s, st);
+    else if (a.k <= 4) launch_knn_k<DIM, 4, FLOAT>(a, s, st);
+    else if (a.k <= 5) launch_knn_k<DIM, 5, FLOAT>(a, s, st);
+    else if (a.k <= 8) launch_knn_k<DIM, 8, FLOAT>(a, s, st);
+    else if (a.k <= 10) launch_knn_k<DIM, 10, FLOAT>(a, s, st);
+    else if (a.k <= 16) launch_knn_k<DIM, 16, FLOAT>(a, s, st);
+    else launch_knn_k<DIM, 32, FLOAT>(a, s, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

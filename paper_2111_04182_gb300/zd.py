@@ -22,6 +22,7 @@ ZD_ERR_NOT_FOUND, ZD_ERR_DUPLICATE_ID, ZD_ERR_TIMEOUT = 5, 6, 7
 ZD_ERR_UNIMPLEMENTED, ZD_ERR_CAPACITY = 8, 9
 ZD_COORD_I32, ZD_COORD_F32 = 0, 1
 ZD_SEARCH_LEAF, ZD_SEARCH_BIT, ZD_SEARCH_ROOT = 0, 1, 2
+ZD_KNN_THREAD_PER_QUERY, ZD_KNN_WARP_GROUP = 0x100, 0x200
 ZD_MAX_K = 32
 
 EXPORTED = ["zd_status_string", "zd_check", "zd_morton_encode", "zd_morton_sort", "zd_build",
@@ -72,7 +73,7 @@ def _lib():
         lib.zd_delete_batch.argtypes = [vp, vp, i64, vp]
         lib.zd_knn_dist_backward.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp, i32, vp, vp, vp]
         lib.zd_build_batched.argtypes = [C.POINTER(ZdParams), vp, vp, vp, vp, i64, vp, C.POINTER(vp)]
-        lib.zd_knn_batched.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp]
+        lib.zd_knn_batched.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("zd_status_string",):
                 getattr(lib, name).restype = C.c_int
@@ -198,9 +199,10 @@ class ZdTree:
         return e
 
     def knn(self, k: int, queries: torch.Tensor = None, mode: int = None, with_dist: bool = True,
-            stream=None, out=None):
+            stream=None, out=None, mapping: int = 0):
         """Exact k-NN (Algorithms 2 and 3), ties by (squared distance, id).
-        queries=None: all points (leaf-based, self excluded), rows by id."""
+        queries=None: all points (leaf-based, self excluded), rows by id.
+        mapping: 0 (library choice), ZD_KNN_THREAD_PER_QUERY or ZD_KNN_WARP_GROUP."""
         if self.batched:
             raise RuntimeError("use zd_knn_batched for a forest")
         ddt = torch.float32 if self.is_float else torch.int64
@@ -218,8 +220,8 @@ class ZdTree:
             dist = torch.empty((rows, k), dtype=ddt, device=self.device) if with_dist else None
         else:
             idx, dist = out
-        _ok(_lib().zd_knn(self.handle, qp, m, k, mode, _ptr(idx), _ptr(dist), C.c_void_p(_stream(stream))),
-            "zd_knn")
+        _ok(_lib().zd_knn(self.handle, qp, m, k, mode | mapping, _ptr(idx), _ptr(dist),
+                          C.c_void_p(_stream(stream))), "zd_knn")
         return idx, dist
 
     def insert(self, pts: torch.Tensor, stream=None) -> torch.Tensor:
@@ -274,7 +276,7 @@ def zd_build_batched(pts: torch.Tensor, offsets, leaf_size: int, coord_bits: int
 
 
 def zd_knn_batched(tree: ZdTree, k: int, queries: torch.Tensor = None, query_offsets=None,
-                   with_dist: bool = True, stream=None, out=None):
+                   with_dist: bool = True, stream=None, out=None, mapping: int = 0):
     """k-NN inside every cloud of a forest; ids are cloud-local."""
     ddt = torch.float32 if tree.is_float else torch.int64
     if queries is None:
@@ -289,8 +291,8 @@ def zd_knn_batched(tree: ZdTree, k: int, queries: torch.Tensor = None, query_off
         dist = torch.empty((rows, k), dtype=ddt, device=tree.device) if with_dist else None
     else:
         idx, dist = out
-    _ok(_lib().zd_knn_batched(tree.handle, qp, _ptr(qo) if qo is not None else None, m, k, _ptr(idx),
-                              _ptr(dist), C.c_void_p(_stream(stream))), "zd_knn_batched")
+    _ok(_lib().zd_knn_batched(tree.handle, qp, _ptr(qo) if qo is not None else None, m, k, mapping,
+                              _ptr(idx), _ptr(dist), C.c_void_p(_stream(stream))), "zd_knn_batched")
     return idx, dist
 
 

@@ -20,7 +20,39 @@ def zd():
     return z
 
 
-def test_batched_all_points_per_cloud(zd, oracle):
+@pytest.mark.parametrize("mapping", [0x100, 0x200])
+def test_batched_tiny_clouds_have_their_own_trees(zd, oracle, mapping):
+    """Clouds smaller than L next to each other: every cloud boundary is a
+    leaf boundary, and each cloud's subtree is that cloud's canonical tree."""
+    from tests._gpu import nodes_of
+    rng = np.random.default_rng(8)
+    sizes = rng.integers(0, 40, size=300)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pts = rng.integers(0, 2 ** 16, size=(int(off[-1]), 3)).astype(np.int32)
+    t = zd.zd_build_batched(torch.from_numpy(pts).to(DEV), off, 16, 16)
+    idx, d2 = zd.zd_knn_batched(t, 5, mapping=mapping)
+    assert zd.zd_check() == 0
+    idx, d2 = idx.cpu().numpy(), d2.cpu().numpy()
+    g = nodes_of(t.export())
+    cloud_bit = 3 * t.info()["coord_bits"]
+    for c in range(300):
+        a, z = int(off[c]), int(off[c + 1])
+        if z == a:
+            continue
+        cloud = pts[a:z]
+        bi, bd = oracle.knn_brute(cloud, 5)
+        assert np.array_equal(idx[a:z], bi) and np.array_equal(d2[a:z], bd), c
+        # the nodes inside this cloud are exactly its own canonical tree
+        inside = (g["lo"] >= a) & (g["hi"] <= z) & (g["bit"] < cloud_bit)
+        got = sorted(zip((g["lo"][inside] - a).tolist(), (g["hi"][inside] - a).tolist(), g["bit"][inside].tolist()))
+        o = oracle.OracleTree(cloud, 16, t.info()["coord_bits"]).canonical_dump()
+        want = sorted(zip(o["lo"].tolist(), o["hi"].tolist(), o["bit"].tolist()))
+        assert got == want, c
+    t.free()
+
+
+@pytest.mark.parametrize("mapping", [0x100, 0x200])
+def test_batched_all_points_per_cloud(zd, oracle, mapping):
     from paper_2111_04182_gb300 import datagen
     w = datagen.workload_batched(n_clouds=40, seed=3, size_range=(1, 9000))
     # drop cloud 4's points: an empty cloud in the middle of the forest
@@ -32,7 +64,7 @@ def test_batched_all_points_per_cloud(zd, oracle):
         off2[c + 1] = off2[c] + sz
     pts = np.concatenate(chunks)
     t = zd.zd_build_batched(torch.from_numpy(pts).to(DEV), off2, 16, 16)
-    idx, d2 = zd.zd_knn_batched(t, 16)
+    idx, d2 = zd.zd_knn_batched(t, 16, mapping=mapping)
     assert zd.zd_check() == 0
     idx, d2 = idx.cpu().numpy(), d2.cpu().numpy()
     for c in range(40):

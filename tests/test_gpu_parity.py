@@ -125,20 +125,40 @@ def test_build_degenerate(zd, oracle):
 
 
 # ------------------------------------------------------------------ kNN
+MAPPINGS = [0x100, 0x200]  # one thread per query; one warp per 32-point group
+
+
+@pytest.mark.parametrize("mapping", MAPPINGS)
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("k", [1, 3, 5, 10, 16, 32])
-def test_knn_all_points(zd, oracle, dim, k):
+def test_knn_all_points(zd, oracle, dim, k, mapping):
     rng = np.random.default_rng(dim * 1000 + k)
     bits = 21 if dim == 3 else 20
     c = rng.integers(0, 2 ** 19, size=(12, dim))
     pts = np.clip(c[rng.integers(0, 12, 40_000)] + rng.normal(0, 2000, (40_000, dim)), 0, 2 ** 19).astype(np.int32)
     pts[:300] = pts[300:600]  # duplicates: ties at d^2 = 0
     t = zd.zd_build(_t(pts), 16, bits)
-    idx, d2 = t.knn(k)
+    idx, d2 = t.knn(k, mapping=mapping)
     assert zd.zd_check() == 0
     oi, od = oracle.OracleTree(pts, 16, bits).knn(k)
     assert np.array_equal(d2.cpu().numpy(), od)
     assert np.array_equal(idx.cpu().numpy(), oi)
+    t.free()
+
+
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_knn_saturated_keys_fall_back_exactly(zd, oracle, mapping):
+    """Far-apart 2D points with 31-bit coordinates: squared distances exceed
+    the packed-key field of the warp-group mapping, whose queries must then
+    be answered by the exact fallback -- the result stays exact."""
+    rng = np.random.default_rng(31)
+    pts = rng.integers(0, 2 ** 31 - 1, size=(3000, 2)).astype(np.int32)
+    pts[:40] = rng.integers(0, 64, size=(40, 2))  # a tight cluster too
+    t = zd.zd_build(_t(pts), 8, 31)
+    idx, d2 = t.knn(6, mapping=mapping)
+    assert zd.zd_check() == 0
+    bi, bd = oracle.knn_brute(pts, 6)
+    assert np.array_equal(idx.cpu().numpy(), bi) and np.array_equal(d2.cpu().numpy(), bd)
     t.free()
 
 
@@ -155,23 +175,26 @@ def test_knn_small_and_padding(zd, oracle):
 
 def test_knn_lattice_ties(zd, oracle):
     g = (np.stack(np.meshgrid(*[np.arange(20)] * 3, indexing="ij"), -1).reshape(-1, 3) * 3).astype(np.int32)
-    t = zd.zd_build(_t(g), 16, 21)
-    idx, d2 = t.knn(10)
     oi, od = oracle.OracleTree(g, 16, 21).knn(10)
-    assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
-    t.free()
+    for shift in (None, [5, 77, 1 << 19]):
+        t = zd.zd_build(_t(g), 16, 21, shift=shift)
+        for mapping in MAPPINGS:
+            idx, d2 = t.knn(10, mapping=mapping)
+            assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+        t.free()
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
 @pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("dim", [2, 3])
-def test_knn_external_queries(zd, oracle, mode, dim):
+def test_knn_external_queries(zd, oracle, mode, dim, mapping):
     rng = np.random.default_rng(mode * 7 + dim)
     bits = 21 if dim == 3 else 20
     pts = rng.integers(0, 2 ** 20, size=(60_000, dim)).astype(np.int32)
     q = rng.integers(0, 2 ** 20, size=(9_001, dim)).astype(np.int32)
     q[:50] = pts[:50]
-    t = zd.zd_build(_t(pts), 16, bits)
-    idx, d2 = t.knn(5, queries=_t(q), mode=mode)
+    t = zd.zd_build(_t(pts), 16, bits, shift=[3, 0, 17][:dim])
+    idx, d2 = t.knn(5, queries=_t(q), mode=mode, mapping=mapping)
     assert zd.zd_check() == 0
     oi, od = oracle.knn_brute(pts, 5, queries=q)
     assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
