@@ -133,6 +133,23 @@ int zd_morton_encode(const zd_params *p, const int32_t *d_pts, int64_t n, uint64
 int zd_morton_sort(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t *d_keys_out,
                    int32_t *d_perm_out, const zd_allocator *alloc, void *stream);
 
+/* zd_morton_sort without allocating: the paper has no counterpart.  It is
+ * for callers that may not allocate device memory on their call path -- a
+ * plug-in running inside a host framework that has reserved the GPU's memory
+ * for its own pool, or a latency-critical loop that must not pay for (or be
+ * serialized by) an allocation.  Same arguments and result as zd_morton_sort,
+ * but all scratch lives in one static device array of this library
+ * (about 26 MB for ZD_NOALLOC_MAX_KEYS keys), which every GPU that loads
+ * the library holds until the process exits; nothing is allocated or freed.
+ * n > ZD_NOALLOC_MAX_KEYS returns ZD_ERR_CAPACITY with no work enqueued.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares
+ * the one array: calls whose work overlaps on the GPU (for example on two
+ * streams) race and corrupt each other; order them on one stream. */
+#define ZD_NOALLOC_MAX_KEYS (1 << 20)
+int zd_morton_sort_noalloc(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t *d_keys_out,
+                           int32_t *d_perm_out, void *stream);
+
 /* ----------------------------------------------------------------- tree -- */
 
 /* Build the canonical pruned zd-tree of n points (Sec. 2 "Construction",

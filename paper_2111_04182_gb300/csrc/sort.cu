@@ -552,3 +552,92 @@ int radix_sort(const u64 *keys_in, int64_t n, int key_bits, u64 *keys_out, int32
 }
 
 } // namespace zdk
+
+// ------------------------------------------------- sort without allocation
+// zd_morton_sort_noalloc: the same passes as radix_sort, with every scratch
+// buffer carved out of one file-scope device array instead of allocated.
+// The array is a static __device__ object of this library, so every GPU
+// that loads the library keeps it until the process exits.
+namespace zdk {
+
+constexpr int64_t NOALLOC_TILES = (ZD_NOALLOC_MAX_KEYS + SORT_TILE - 1) / SORT_TILE;
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t NA_HIST = 0;
+constexpr size_t NA_PLAN = na_align(NA_HIST + sizeof(u32) * MAX_PASSES * RADIX);
+constexpr size_t NA_LB = na_align(NA_PLAN + sizeof(SortPlan));
+constexpr size_t NA_LB_WORDS = (size_t)MAX_PASSES * NOALLOC_TILES * RADIX + MAX_PASSES;
+constexpr size_t NA_K0 = na_align(NA_LB + sizeof(u32) * NA_LB_WORDS);
+constexpr size_t NA_K1 = NA_K0 + sizeof(u64) * ZD_NOALLOC_MAX_KEYS;
+constexpr size_t NA_V0 = NA_K1 + sizeof(u64) * ZD_NOALLOC_MAX_KEYS;
+constexpr size_t NA_V1 = NA_V0 + sizeof(u32) * ZD_NOALLOC_MAX_KEYS;
+constexpr size_t NA_BYTES = NA_V1 + sizeof(u32) * ZD_NOALLOC_MAX_KEYS;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// Device address of the scratch array on the current device.  In host code
+// the symbol itself is only a host-side stand-in, so the address is looked
+// up once per device (cudaGetSymbolAddress, with that device current) and
+// cached.
+static unsigned char *noalloc_scratch()
+{
+    static unsigned char *addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+        addr[dev] = (unsigned char *)p;
+    }
+    return addr[dev];
+}
+
+} // namespace zdk
+
+extern "C" int zd_morton_sort_noalloc(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t *d_keys_out,
+                                      int32_t *d_perm_out, void *stream)
+{
+    using namespace zdk;
+    if (n < 0 || key_bits < 1 || key_bits > 64) return ZD_ERR_INVALID_ARG;
+    if (n > ZD_NOALLOC_MAX_KEYS) return ZD_ERR_CAPACITY;
+    if (n > 0 && (!d_keys_in || !d_keys_out || !d_perm_out)) return ZD_ERR_INVALID_ARG;
+    unsigned char *base = noalloc_scratch();
+    u32 *status = status_word();
+    if (!base || !status) return ZD_ERR_CUDA;
+    if (n == 0) return ZD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const u64 *keys_in = (const u64 *)d_keys_in;
+    const int npasses = (key_bits + RADIX_BITS - 1) / RADIX_BITS;
+    const int64_t num_tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    u32 *hist = (u32 *)(base + NA_HIST);
+    SortPlan *plan = (SortPlan *)(base + NA_PLAN);
+    u32 *lookback = (u32 *)(base + NA_LB);
+    u32 *tile_counter = lookback + (size_t)npasses * num_tiles * RADIX;
+    // the array keeps the previous call's contents: clear what counts
+    ZD_CUDA(cudaMemsetAsync(hist, 0, sizeof(u32) * MAX_PASSES * RADIX, s));
+    ZD_CUDA(cudaMemsetAsync(lookback, 0, sizeof(u32) * ((size_t)npasses * num_tiles * RADIX + MAX_PASSES), s));
+    k_hist<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(keys_in, n, hist, npasses);
+    k_sort_plan<<<1, 256, 0, s>>>(hist, n, npasses, plan);
+    ZD_CUDA(cudaGetLastError());
+    ZD_CUDA(cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem()));
+    PassArgs a;
+    a.keys_in = keys_in;
+    a.ktmp[0] = (u64 *)(base + NA_K0);
+    a.ktmp[1] = (u64 *)(base + NA_K1);
+    a.vtmp[0] = (u32 *)(base + NA_V0);
+    a.vtmp[1] = (u32 *)(base + NA_V1);
+    a.keys_out = (u64 *)d_keys_out;
+    a.vals_out = (u32 *)d_perm_out;
+    a.n = n;
+    a.plan = plan;
+    a.lookback = lookback;
+    a.tile_counter = tile_counter;
+    a.num_tiles = num_tiles;
+    a.status = status;
+    for (int p = 0; p < npasses; ++p) {
+        k_onesweep<<<(unsigned)num_tiles, SORT_THREADS, onesweep_smem(), s>>>(a, p);
+        ZD_CUDA(cudaGetLastError());
+    }
+    k_sort_finish<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(plan, keys_in, n, (u64 *)d_keys_out, (u32 *)d_perm_out);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}

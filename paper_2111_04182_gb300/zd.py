@@ -25,7 +25,8 @@ ZD_SEARCH_LEAF, ZD_SEARCH_BIT, ZD_SEARCH_ROOT = 0, 1, 2
 ZD_KNN_THREAD_PER_QUERY, ZD_KNN_WARP_GROUP = 0x100, 0x200
 ZD_MAX_K = 32
 
-EXPORTED = ["zd_status_string", "zd_check", "zd_morton_encode", "zd_morton_sort", "zd_build",
+EXPORTED = ["zd_status_string", "zd_check", "zd_morton_encode", "zd_morton_sort", "zd_morton_sort_noalloc",
+            "zd_build",
             "zd_free", "zd_tree_info_get", "zd_export_tree", "zd_knn", "zd_insert_batch",
             "zd_delete_batch", "zd_knn_dist_backward", "zd_build_batched", "zd_knn_batched"]
 
@@ -64,6 +65,7 @@ def _lib():
         lib.zd_check.argtypes = [vp]
         lib.zd_morton_encode.argtypes = [C.POINTER(ZdParams), vp, i64, vp, vp]
         lib.zd_morton_sort.argtypes = [vp, i64, i32, vp, vp, vp, vp]
+        lib.zd_morton_sort_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
         lib.zd_build.argtypes = [C.POINTER(ZdParams), vp, vp, i64, vp, C.POINTER(vp)]
         lib.zd_free.argtypes = [vp, vp]
         lib.zd_tree_info_get.argtypes = [vp, C.POINTER(ZdTreeInfo), vp]
@@ -139,6 +141,23 @@ def zd_morton_sort(keys: torch.Tensor, key_bits: int = 64, stream=None):
     _ok(_lib().zd_morton_sort(_ptr(keys), n, key_bits, _ptr(out), _ptr(perm), None,
                               C.c_void_p(_stream(stream))), "zd_morton_sort")
     return out, perm
+
+
+ZD_NOALLOC_MAX_KEYS = 1 << 20
+
+
+def zd_morton_sort_noalloc(keys: torch.Tensor, key_bits: int = 64, stream=None, out=None):
+    """zd_morton_sort for callers that may not allocate device memory: the
+    library uses its own static scratch (at most ZD_NOALLOC_MAX_KEYS keys).
+    Pass preallocated `out=(keys_out, perm_out)` to allocate nothing here
+    either.  Calls that overlap on the GPU share the scratch and race."""
+    keys = _cuda(keys, torch.int64, "keys")
+    n = keys.numel()
+    if out is None:
+        out = (torch.empty_like(keys), torch.empty(n, dtype=torch.int32, device=keys.device))
+    _ok(_lib().zd_morton_sort_noalloc(_ptr(keys), n, key_bits, _ptr(out[0]), _ptr(out[1]),
+                                      C.c_void_p(_stream(stream))), "zd_morton_sort_noalloc")
+    return out
 
 
 class ZdTree:
