@@ -67,7 +67,8 @@ def source_digest(files) -> str:
     return h.hexdigest()[:12]
 
 
-KNN_SOURCES = ["paper_2111_04182_gb300/csrc/knn_impl.cuh", "paper_2111_04182_gb300/csrc/knn_i32.cu"]
+KNN_SOURCES = ["paper_2111_04182_gb300/csrc/knn_impl.cuh", "paper_2111_04182_gb300/csrc/knn_group.cuh",
+               "paper_2111_04182_gb300/csrc/knn_i32.cu"]
 
 
 def profiled_traffic(kernel: str, workload: str):
@@ -255,9 +256,12 @@ def run_ours(args):
     knn_avg = sum(knn_ms) / len(knn_ms)
     build_avg = sum(build_ms) / len(build_ms)
     achieved = kb / (knn_avg / 1e3) / 1e9
-    traffic = profiled_traffic("k_knn", "3d-clustered-1e7") if n == 10_000_000 else None
+    traffic = profiled_traffic("k_knn_group", "3d-clustered-1e7") if n == 10_000_000 else None
     bb = build_bytes_per_point() * n
-    launches_per_step = 20  # encode, plan, 8 sort passes, finish, gather, 5 topology, 2 id-table fills, knn
+    # build: 2 id-table fills, encode, plan, 8 sort passes, finish, gather,
+    # split flags, scan, leaf index, internal nodes, boxes, float copy (20);
+    # k-NN: warp groups + exact fallback (2)
+    launches_per_step = 22
     out = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -269,7 +273,7 @@ def run_ours(args):
         "components": {"build_ms": build_avg, "build_pts_per_s": n / (build_avg / 1e3),
                        "build_hbm_frac": bb / (build_avg / 1e3) / 1e9 / pk,
                        "knn_ms": knn_avg, "knn_queries_per_s": n / (knn_avg / 1e3)},
-        "roofline": {"kernel": "k_knn<3,10,int>", "bound": "hbm", "achieved": achieved, "peak": pk,
+        "roofline": {"kernel": "k_knn_group<3,10,fs>", "bound": "hbm", "achieved": achieved, "peak": pk,
                      "peak_source": pk_src, "unit": "GB/s", "frac": achieved / pk,
                      "traffic": traffic, "algorithmic_bytes_per_launch": kb},
         "clocks": clk,
