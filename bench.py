@@ -342,11 +342,195 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
 def run_other(args, ws, rank, local):
-    from bench_workloads import run_workload  # noqa: E402
-    out = run_workload(args)
+    fn = {"2d-uniform": bench_2d, "dynamic": bench_dynamic, "batched": bench_batched,
+          "differentiable": bench_differentiable}.get(args.workload)
+    if fn is None:
+        raise SystemExit("unknown workload %r" % args.workload)
+    out = fn(args)
+    out["n_gpus"] = ws
     if rank == 0:
         print(json.dumps(out))
+
+
+def bench_2d(args):
+    """2D uniform, n = 100,000, L = 16, k = 10: build + all-points k-NN."""
+    import torch
+    from paper_2111_04182_gb300 import datagen, zd
+    w = datagen.workload_2d_uniform()
+    n, k = len(w["pts"]), w["k"]
+    pts = torch.from_numpy(w["pts"]).cuda()
+    idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((n, k), dtype=torch.int64, device="cuda")
+    for _ in range(args.warmup):
+        t = zd.zd_build(pts, w["leaf_size"], w["coord_bits"]); t.knn(k, out=(idx, d2)); t.free()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        a, b, c = _events(3)
+        a.record(); t = zd.zd_build(pts, w["leaf_size"], w["coord_bits"]); b.record()
+        t.knn(k, out=(idx, d2)); c.record(); c.synchronize(); t.free()
+        ms.append((a.elapsed_time(b), b.elapsed_time(c)))
+    assert zd.zd_check() == 0
+    bm = float(np.median([m[0] for m in ms])); km = float(np.median([m[1] for m in ms]))
+    return {"workload": "2d-uniform-1e5", "metric": "queries/s (build + all-points k=10)",
+            "value": n / ((bm + km) / 1e3), "unit": "queries/s", "build_ms": bm, "knn_ms": km,
+            "build_pts_per_s": n / (bm / 1e3), "knn_queries_per_s": n / (km / 1e3), "steps": args.steps}
+
+
+def bench_dynamic(args):
+    """5e7 uniform points; rounds of +1e6 insert, -1e6 delete, 1e6 queries
+    (k = 5, bit-based); every round checked against the oracle's brute force
+    on sampled queries."""
+    import torch
+    from oracle import oracle
+    from paper_2111_04182_gb300 import datagen, zd
+    rounds = args.rounds
+    w = datagen.DynamicWorkload(n0=args.dyn_n0, batch=args.dyn_batch, n_queries=args.dyn_batch, rounds=rounds)
+    cap = w.n0 + w.batch
+    all_pts = np.empty((w.n0 + rounds * w.batch, 3), np.int32)
+    all_pts[: w.n0] = w.initial
+    pts = torch.from_numpy(w.initial).cuda()
+    a, b = _events(2)
+    a.record(); t = zd.zd_build(pts, w.leaf_size, w.coord_bits, capacity=cap); b.record(); b.synchronize()
+    build_ms = a.elapsed_time(b)
+    del pts
+    ins_ms, del_ms, q_ms, checked = [], [], [], 0
+    rng = np.random.default_rng(7)
+    for r in range(rounds):
+        ins, dele, q = w.round()
+        ins_d, del_d, q_d = torch.from_numpy(ins).cuda(), torch.from_numpy(dele).cuda(), torch.from_numpy(q).cuda()
+        torch.cuda.synchronize()
+        e = _events(6)
+        e[0].record(); new = t.insert(ins_d); e[1].record()
+        e[2].record(); t.delete(del_d); e[3].record()
+        e[4].record(); idx, d2 = t.knn(w.k, queries=q_d, mode=zd.ZD_SEARCH_BIT); e[5].record()
+        e[5].synchronize()
+        ins_ms.append(e[0].elapsed_time(e[1])); del_ms.append(e[2].elapsed_time(e[3])); q_ms.append(e[4].elapsed_time(e[5]))
+        all_pts[new.cpu().numpy()] = ins
+        # oracle check of sampled queries against the live set
+        live = w.live.astype(np.int64)
+        sel = rng.choice(len(q), size=args.dyn_check, replace=False)
+        bi, bd = oracle.knn_brute(all_pts[live], w.k, queries=q[sel], ref_ids=live.astype(np.int32))
+        if not (np.array_equal(idx.cpu().numpy()[sel], bi) and np.array_equal(d2.cpu().numpy()[sel], bd)):
+            raise RuntimeError("round %d: k-NN differs from the oracle" % r)
+        checked += len(sel)
+    assert zd.zd_check() == 0
+    im, dm, qm = (float(np.median(x)) for x in (ins_ms, del_ms, q_ms))
+    t.free()
+    return {"workload": "dynamic-5e7", "metric": "updates/s (insert, delete) and queries/s", "unit": "updates/s",
+            "value": w.batch / (im / 1e3), "insert_per_s": w.batch / (im / 1e3), "delete_per_s": w.batch / (dm / 1e3),
+            "query_per_s": w.batch / (qm / 1e3), "insert_ms": im, "delete_ms": dm, "query_ms": qm,
+            "initial_build_ms": build_ms, "rounds": rounds, "oracle_checked_queries": checked, "k": w.k}
+
+
+def bench_batched(args):
+    """4096 clouds (1024..65536 points each), all-points k = 16 in every cloud:
+    leaf size and thread mapping autotuned; the whole step (forest build +
+    search + free) captured in one CUDA graph and replayed."""
+    import torch
+    from paper_2111_04182_gb300 import autotune, datagen, zd
+    w = datagen.workload_batched(n_clouds=args.clouds)
+    pts = torch.from_numpy(w["pts"]).cuda()
+    off = w["offsets"]
+    n, k, B = int(off[-1]), w["k"], w["coord_bits"]
+    idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((n, k), dtype=torch.int64, device="cuda")
+    tune = autotune.tune_batched(pts, off, k, B, out=(idx, d2), use_cache=False)
+    L, mp = tune["leaf_size"], tune["mapping"]
+
+    off_d = torch.from_numpy(off).cuda()
+
+    def step():
+        t = zd.zd_build_batched(pts, off, L, B, offsets_device=off_d)
+        zd.zd_knn_batched(t, k, out=(idx, d2), mapping=mp)
+        t.free()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    graph = None
+    try:
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            step()
+            torch.cuda.synchronize()
+            g.capture_begin()
+            step()
+            g.capture_end()
+        torch.cuda.current_stream().wait_stream(s)
+        graph = g
+    except Exception as e:  # report, and time the eager step instead
+        graph_error = repr(e)
+        torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        a, b = _events(2)
+        a.record()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+        b.record(); b.synchronize()
+        ms.append(a.elapsed_time(b))
+    assert zd.zd_check() == 0
+    m = float(np.median(ms))
+    out = {"workload": "batched-4096", "metric": "clouds/s, points/s (build + all-points k=16 per cloud)",
+           "value": (len(off) - 1) / (m / 1e3), "unit": "clouds/s", "ms_per_step": m,
+           "points_per_s": n / (m / 1e3), "queries_per_s": n / (m / 1e3), "n_points": n, "k": k,
+           "leaf_size": L, "mapping": tune["mapping_name"], "tuning": tune["table"],
+           "graph": graph is not None, "graph_launches_per_step": 1 if graph is not None else None}
+    if graph is None:
+        out["graph_error"] = graph_error
+    return out
+
+
+def bench_differentiable(args):
+    """64 pairs of float clouds (A 16384, B 32768): k = 8 neighbours in B for
+    every point of A (fp64 ranking), loss = sum of fp32 distances, backward to
+    A and B."""
+    import torch
+    from oracle import oracle
+    from paper_2111_04182_gb300 import datagen, zd
+    w = datagen.workload_differentiable()
+    A = torch.from_numpy(w["A"]).cuda().requires_grad_(True)
+    B = torch.from_numpy(w["B"]).cuda().requires_grad_(True)
+    k = w["k"]
+
+    def step():
+        A.grad = None
+        B.grad = None
+        dist, idx = zd.KnnDist.apply(A, B, k, w["leaf_size"], w["coord_bits"])
+        dist.sum().backward()
+        return idx
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        a, b = _events(2)
+        a.record(); idx = step(); b.record(); b.synchronize()
+        ms.append(a.elapsed_time(b))
+    assert zd.zd_check() == 0
+    m = float(np.median(ms))
+    # accuracy against the fp64 oracle on one pair
+    p = 0
+    bi, _ = oracle.knn_brute(w["B"][p], k, queries=w["A"][p])
+    same = bool(np.array_equal(idx[p].cpu().numpy(), bi))
+    _, ga, gb = oracle.knn_dist_grad(w["A"][p], w["B"][p], bi)
+    rel = lambda g, g64: float(np.max(np.abs(g - g64)) / max(np.max(np.abs(g64)), 1e-3))
+    return {"workload": "differentiable-64x16384x32768", "metric": "fwd+bwd/s", "value": 1e3 / m,
+            "unit": "fwd+bwd/s", "ms_per_step": m, "pairs_per_s": 64 * 1e3 / m, "queries_per_s": 64 * 16384 * 1e3 / m,
+            "k": k, "ids_match_fp64_oracle_pair0": same,
+            "grad_rel_err_vs_fp64": {"A": rel(A.grad[p].cpu().numpy(), ga), "B": rel(B.grad[p].cpu().numpy(), gb)}}
 
 
 def main():
@@ -359,6 +543,11 @@ def main():
     ap.add_argument("--n", type=int, default=10_000_000)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rounds", type=int, default=20)
+    ap.add_argument("--dyn-n0", type=int, default=50_000_000)
+    ap.add_argument("--dyn-batch", type=int, default=1_000_000)
+    ap.add_argument("--dyn-check", type=int, default=16)
+    ap.add_argument("--clouds", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -275,14 +275,16 @@ def zd_build(pts: torch.Tensor, leaf_size: int, coord_bits: int, shift=None, cap
     return ZdTree(h, dim, ct == ZD_COORD_F32, False, pts.device)
 
 
-def zd_build_batched(pts: torch.Tensor, offsets, leaf_size: int, coord_bits: int, stream=None) -> ZdTree:
+def zd_build_batched(pts: torch.Tensor, offsets, leaf_size: int, coord_bits: int, stream=None,
+                     offsets_device: torch.Tensor = None) -> ZdTree:
     """One forest of independent trees; offsets [n_clouds + 1] (host list /
-    CPU tensor or CUDA tensor)."""
+    CPU tensor).  offsets_device: the same offsets already on the GPU (pass it
+    when capturing a CUDA graph, so that no host copy is recorded)."""
     pts = pts.contiguous()
     ct = ZD_COORD_F32 if pts.dtype == torch.float32 else ZD_COORD_I32
     n, dim = pts.shape
     off_h = torch.as_tensor(offsets, dtype=torch.int64).cpu().contiguous()
-    off_d = off_h.to(pts.device)
+    off_d = offsets_device if offsets_device is not None else off_h.to(pts.device)
     p = _params(dim, leaf_size, coord_bits, ct)
     h = C.c_void_p()
     t = ZdTree(None, dim, ct == ZD_COORD_F32, True, pts.device)

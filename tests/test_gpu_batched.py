@@ -95,3 +95,48 @@ def test_batched_external_float_queries(zd, oracle):
         bi, bd = oracle.knn_brute(B[p], 8, queries=A[p])
         assert np.array_equal(idx[offA[p]:offA[p + 1]], bi), p
     t.free()
+
+
+def test_batched_step_in_cuda_graph_matches_eager(zd, oracle):
+    """The whole forest step (build + all-points search + free) captured in
+    one CUDA graph and replayed gives the eager answer."""
+    from paper_2111_04182_gb300 import autotune, datagen
+    w = datagen.workload_batched(n_clouds=64, seed=11, size_range=(100, 5000))
+    pts = torch.from_numpy(w["pts"]).to(DEV)
+    off = w["offsets"]
+    off_d = torch.from_numpy(off).to(DEV)
+    n = int(off[-1])
+    tune = autotune.tune_batched(pts, off, 16, 16, use_cache=False, reps=1)
+    assert tune["leaf_size"] in autotune.LEAF_SIZES and len(tune["table"]) == 6
+    L, mp = tune["leaf_size"], tune["mapping"]
+    idx = torch.full((n, 16), -7, dtype=torch.int32, device=DEV)
+    d2 = torch.full((n, 16), -7, dtype=torch.int64, device=DEV)
+
+    def step():
+        t = zd.zd_build_batched(pts, off, L, 16, offsets_device=off_d)
+        zd.zd_knn_batched(t, 16, out=(idx, d2), mapping=mp)
+        t.free()
+
+    step()
+    torch.cuda.synchronize()
+    ref_i, ref_d = idx.clone(), d2.clone()
+    idx.fill_(-7)
+    d2.fill_(-7)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        step()
+        g.capture_end()
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        idx.fill_(-7)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(idx, ref_i) and torch.equal(d2, ref_d)
+    assert zd.zd_check() == 0
+    c = 3
+    a, z = int(off[c]), int(off[c + 1])
+    bi, bd = oracle.knn_brute(w["pts"][a:z], 16)
+    assert np.array_equal(ref_i[a:z].cpu().numpy(), bi)
