@@ -154,13 +154,22 @@ def barrier(ws):
 
 
 def max_over_ranks(x: float, ws: int) -> float:
+    """The slowest rank's time (all ranks get it)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: int, local_ms: float, ws: int):
+    """Replicas: every rank processes units_per_rank; the job's rate is all
+    units over the slowest rank's time.  Returns (units/s, max ms)."""
+    ms = max_over_ranks(local_ms, ws)
+    return ws * units_per_rank / (ms / 1e3), ms
 
 
 # ------------------------------------------------------------------ ours
@@ -224,8 +233,7 @@ def run_ours(args):
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     knn_ms = [e[1].elapsed_time(e[2]) for e in evs]
     step_ms = sum(b + q for b, q in zip(build_ms, knn_ms)) / args.steps
-    step_ms = max_over_ranks(step_ms, ws)
-    value = ws * n / (step_ms / 1e3)
+    value, step_ms = weak_scaling_value(n, step_ms, ws)
 
     # end to end through the public API with host buffers
     idx_h = torch.empty((n, k), dtype=torch.int32).pin_memory()

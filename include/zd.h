@@ -114,6 +114,14 @@ const char *zd_status_string(int status);
  * first data-dependent error recorded since the last zd_check, or ZD_OK. */
 int zd_check(void *stream);
 
+/* Failure-detection check (no counterpart in the paper).  Launches one warp
+ * that waits on a device flag that nothing ever sets, through the same
+ * bounded wait that guards every device-side wait of the library (the radix
+ * sort's look-back).  The wait gives up after timeout_ms (1..2000) and
+ * records ZD_ERR_TIMEOUT, so a following zd_check returns ZD_ERR_TIMEOUT and
+ * the context stays usable.  Nothing faults or hangs. */
+int zd_selftest_wait_timeout(int timeout_ms, void *stream);
+
 /* ---------------------------------------------------------------- steps -- */
 
 /* Morton keys (Sec. 1.1 "Morton ordering"; shift of Sec. 2 "Construction").

@@ -34,6 +34,33 @@ __device__ __forceinline__ void set_status(u32 *status, int code)
 // Host: address of this device's status word (looked up once per device).
 u32 *status_word();
 
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every device-side wait of the library goes through this: poll *p until a
+// bit of `mask` is set, backing off with __nanosleep, and give up after
+// timeout_ns of wall time or max_polls polls.  Returns false on giving up;
+// the caller then records ZD_ERR_TIMEOUT and carries on so the kernel ends
+// and the context stays usable.
+__device__ __forceinline__ bool wait_for_flag(const volatile u32 *p, u32 mask, unsigned long long timeout_ns,
+                                              int max_polls, u32 &w)
+{
+    w = *p;
+    if (w & mask) return true;
+    const unsigned long long t0 = globaltimer();
+    int polls = 0;
+    while (!((w = *p) & mask)) {
+        ++polls;
+        if (polls > 32) __nanosleep(64);
+        if (polls >= max_polls || ((polls & 1023) == 0 && globaltimer() - t0 > timeout_ns)) return false;
+    }
+    return true;
+}
+
 // ----------------------------------------------------------------- memory
 struct Mem {
     const zd_allocator *a;

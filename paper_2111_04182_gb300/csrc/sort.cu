@@ -294,12 +294,6 @@ struct SortPlan {
     int Q;                      // passes that run
 };
 
-__device__ __forceinline__ u64 globaltimer()
-{
-    u64 t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Exclusive scan of one value per thread over a 256-thread block.
 __device__ __forceinline__ u32 block_excl_scan256(u32 v, u32 *s_warp /* [8] */)
@@ -433,20 +427,10 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(PassArgs a, int pass)
         int64_t t = tile - 1;
         for (;;) {
             volatile const u32 *p = lb + t * RADIX + d;
-            u32 w = *p;
-            if (!(w & ~LB_COUNT)) {
-                u64 t0 = globaltimer();
-                int polls = 0;
-                while (!((w = *p) & ~LB_COUNT)) {
-                    ++polls;
-                    if (polls > 32) __nanosleep(64);
-                    if (polls >= LB_MAX_POLLS ||
-                        ((polls & 1023) == 0 && globaltimer() - t0 > LB_TIMEOUT_NS)) {
-                        set_status(a.status, ZD_ERR_TIMEOUT);
-                        w = LB_INC; // give up: treat as complete so the pass ends
-                        break;
-                    }
-                }
+            u32 w;
+            if (!wait_for_flag(p, ~LB_COUNT, LB_TIMEOUT_NS, LB_MAX_POLLS, w)) {
+                set_status(a.status, ZD_ERR_TIMEOUT);
+                w = LB_INC; // give up: treat as complete so the pass ends
             }
             prefix += w & LB_COUNT;
             if ((w & ~LB_COUNT) == LB_INC || t == 0) break;
@@ -638,6 +622,30 @@ extern "C" int zd_morton_sort_noalloc(const uint64_t *d_keys_in, int64_t n, int 
         ZD_CUDA(cudaGetLastError());
     }
     k_sort_finish<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(plan, keys_in, n, (u64 *)d_keys_out, (u32 *)d_perm_out);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+// ------------------------------------------------ failure-detection check
+namespace zdk {
+static __device__ u32 g_never_set; // no code ever writes it
+
+__global__ void k_wait_selftest(const u32 *flag, unsigned long long timeout_ns, u32 *status)
+{
+    u32 w;
+    if (!wait_for_flag(flag, 0xffffffffu, timeout_ns, LB_MAX_POLLS, w)) set_status(status, ZD_ERR_TIMEOUT);
+}
+} // namespace zdk
+
+extern "C" int zd_selftest_wait_timeout(int timeout_ms, void *stream)
+{
+    using namespace zdk;
+    if (timeout_ms < 1 || timeout_ms > 2000) return ZD_ERR_INVALID_ARG;
+    u32 *status = status_word();
+    void *flag = nullptr;
+    if (!status || cudaGetSymbolAddress(&flag, g_never_set) != cudaSuccess) return ZD_ERR_CUDA;
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>((const u32 *)flag, (unsigned long long)timeout_ms * 1000000ull,
+                                                       status);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

@@ -25,7 +25,7 @@ ZD_SEARCH_LEAF, ZD_SEARCH_BIT, ZD_SEARCH_ROOT = 0, 1, 2
 ZD_KNN_THREAD_PER_QUERY, ZD_KNN_WARP_GROUP = 0x100, 0x200
 ZD_MAX_K = 32
 
-EXPORTED = ["zd_status_string", "zd_check", "zd_morton_encode", "zd_morton_sort", "zd_morton_sort_noalloc",
+EXPORTED = ["zd_status_string", "zd_check", "zd_selftest_wait_timeout", "zd_morton_encode", "zd_morton_sort", "zd_morton_sort_noalloc",
             "zd_build",
             "zd_free", "zd_tree_info_get", "zd_export_tree", "zd_knn", "zd_insert_batch",
             "zd_delete_batch", "zd_knn_dist_backward", "zd_build_batched", "zd_knn_batched"]
@@ -63,6 +63,7 @@ def _lib():
         lib.zd_status_string.argtypes = [i32]
         lib.zd_status_string.restype = C.c_char_p
         lib.zd_check.argtypes = [vp]
+        lib.zd_selftest_wait_timeout.argtypes = [i32, vp]
         lib.zd_morton_encode.argtypes = [C.POINTER(ZdParams), vp, i64, vp, vp]
         lib.zd_morton_sort.argtypes = [vp, i64, i32, vp, vp, vp, vp]
         lib.zd_morton_sort_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
@@ -118,6 +119,12 @@ def _params(dim, leaf_size, coord_bits, coord_type, shift=None, capacity=0) -> Z
 def zd_check(stream=None) -> int:
     """Sync the stream; return and clear the device status word."""
     return _lib().zd_check(C.c_void_p(_stream(stream)))
+
+
+def zd_selftest_wait_timeout(timeout_ms: int = 50, stream=None) -> None:
+    """Enqueue a bounded wait on a flag nothing sets (failure-detection check);
+    the next zd_check returns ZD_ERR_TIMEOUT."""
+    _ok(_lib().zd_selftest_wait_timeout(int(timeout_ms), C.c_void_p(_stream(stream))), "zd_selftest_wait_timeout")
 
 
 def zd_morton_encode(pts: torch.Tensor, coord_bits: int, shift=None, stream=None) -> torch.Tensor:
