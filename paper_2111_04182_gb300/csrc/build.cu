@@ -346,8 +346,12 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
         lbox[2 * j] = lo;
         lbox[2 * j + 1] = hi;
         if (flbox) {
-            flbox[2 * j] = as_float4(lo);
-            flbox[2 * j + 1] = as_float4(hi);
+            // spare w lanes: the leaf's range of sorted positions
+            float4 flo = as_float4(lo), fhi = as_float4(hi);
+            flo.w = __int_as_float(leaf_lo[j]);
+            fhi.w = __int_as_float(leaf_lo[j + 1]);
+            flbox[2 * j] = flo;
+            flbox[2 * j + 1] = fhi;
         }
         __threadfence();
         int p = lparent[j];
@@ -362,8 +366,12 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
             ibox[2 * p] = lo2;
             ibox[2 * p + 1] = hi2;
             if (fibox) {
-                fibox[2 * p] = as_float4(lo2);
-                fibox[2 * p + 1] = as_float4(hi2);
+                // spare w lanes: the two children
+                float4 flo = as_float4(lo2), fhi = as_float4(hi2);
+                flo.w = __int_as_float(ch.x);
+                fhi.w = __int_as_float(ch.y);
+                fibox[2 * p] = flo;
+                fibox[2 * p + 1] = fhi;
             }
             __threadfence();
             p = iparent[p];

@@ -221,9 +221,12 @@ __device__ __forceinline__ void group_search(const TreeView &t, int start, int l
         __syncwarp();
         if (v < 0 && ~v >= l0 && ~v <= l1) continue; // scanned already
         bool need;
+        float4 flo, fhi;
         if (FS) {
             const float4 *fb = v < 0 ? t.flbox + 2 * (~v) : t.fibox + 2 * v;
-            need = c.live && box_d2f<DIM>(c, __ldg(fb), __ldg(fb + 1)) <= thr_f;
+            flo = __ldg(fb);
+            fhi = __ldg(fb + 1);
+            need = c.live && box_d2f<DIM>(c, flo, fhi) <= thr_f;
         } else {
             int4 lo, hi;
             node_box(t, v, lo, hi);
@@ -231,12 +234,15 @@ __device__ __forceinline__ void group_search(const TreeView &t, int start, int l
         }
         if (!__any_sync(0xffffffffu, need)) continue;
         if (v < 0) {
-            const int a = __ldg(t.leaf_lo + ~v), b = __ldg(t.leaf_lo + ~v + 1);
-            if (FS) group_scan_f<DIM, K>(t, a, b, c, key, thr, thr_f);
-            else group_scan<DIM, K>(t, a, b, c, key, thr);
+            if (FS) {
+                group_scan_f<DIM, K>(t, __float_as_int(flo.w), __float_as_int(fhi.w), c, key, thr, thr_f);
+            } else {
+                const int a = __ldg(t.leaf_lo + ~v), b = __ldg(t.leaf_lo + ~v + 1);
+                group_scan<DIM, K>(t, a, b, c, key, thr);
+            }
             continue;
         }
-        const int2 ch = __ldg(t.ichild + v);
+        const int2 ch = FS ? make_int2(__float_as_int(flo.w), __float_as_int(fhi.w)) : __ldg(t.ichild + v);
         const bool right_first = (mid_key >> __ldg(t.ibit + v)) & 1;
         if (sp + 2 > GROUP_STACK) {
             if (lane == 0) set_status(status, ZD_ERR_CUDA);

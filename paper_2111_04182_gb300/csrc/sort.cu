@@ -352,10 +352,13 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(PassArgs a, int pass)
     const int q = a.plan->qidx[pass];
     if (q < 0) return; // every key has the same digit: nothing to do
     const int Q = a.plan->Q;
-    const u64 *ksrc = q == 0 ? a.keys_in : a.ktmp[(q - 1) & 1];
-    const u32 *vsrc = q == 0 ? nullptr : a.vtmp[(q - 1) & 1];
-    u64 *kdst = q == Q - 1 ? a.keys_out : a.ktmp[q & 1];
-    u32 *vdst = q == Q - 1 ? a.vals_out : a.vtmp[q & 1];
+    // (selects, not indexing: a runtime index into the parameter arrays would
+    // copy the parameters to local memory)
+    const bool odd = q & 1;
+    const u64 *ksrc = q == 0 ? a.keys_in : (odd ? a.ktmp[0] : a.ktmp[1]);
+    const u32 *vsrc = q == 0 ? nullptr : (odd ? a.vtmp[0] : a.vtmp[1]);
+    u64 *kdst = q == Q - 1 ? a.keys_out : (odd ? a.ktmp[1] : a.ktmp[0]);
+    u32 *vdst = q == Q - 1 ? a.vals_out : (odd ? a.vtmp[1] : a.vtmp[0]);
     const int shift = pass * RADIX_BITS;
 
     extern __shared__ __align__(16) unsigned char smem[];
