@@ -78,8 +78,9 @@ struct zd_tree {
     float4 *fpts, *fibox, *flbox; // integer trees with B <= 24: exact float copies
     double *frame;      // float trees: [n_clouds * 4]
     int64_t *cloud_off; // forests: [n_clouds + 1]
-    u32 *alive;         // dynamic trees: per id, 1 = live, 2 = marked for delete
-    int64_t id_cap;
+    u32 *alive;         // dynamic trees: live bits [0, W), marked bits [W, 2W), W = id_words
+    int64_t id_cap;     // ids the bitmaps cover (a multiple of 32)
+    int64_t id_words;
     int64_t max_cloud;  // largest cloud (forests): bounds the local ids
     int *group_start;   // forests: first sorted position of every 32-point group
     int64_t n_groups;
@@ -243,11 +244,28 @@ static int build_core(zd_tree *t, const void *d_pts, const int64_t *seg_off, int
     return m.failed ? ZD_ERR_OOM : ZD_OK;
 }
 
-__global__ void k_fill_u32(u32 *p, int64_t a, int64_t z, u32 v)
+// Liveness bitmaps of a fresh tree: ids [0, n) live, nothing marked.
+__global__ void k_init_bits(u32 *bits, int64_t words, int64_t n)
 {
-    for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < z;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = v;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < 2 * words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        u32 v = 0;
+        if (w < words) {
+            const int64_t lo = 32 * w;
+            v = lo + 32 <= n ? 0xffffffffu : (lo < n ? (1u << (n - lo)) - 1u : 0u);
+        }
+        bits[w] = v;
+    }
+}
+
+// Copy both bitmaps into larger ones (new words zero).
+__global__ void k_grow_bits(const u32 *old, int64_t ow, u32 *nw_bits, int64_t nw)
+{
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < 2 * nw;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t half = w < nw ? 0 : 1, i = w - half * nw;
+        nw_bits[w] = i < ow ? old[half * ow + i] : 0u;
+    }
 }
 
 extern "C" {
@@ -332,11 +350,11 @@ int zd_build(const zd_params *p, const zd_allocator *alloc, const void *d_pts, i
     Mem m = mem_of(t, s);
     int r = tree_arrays(t, m, dynamic);
     if (r == ZD_OK && dynamic) {
-        t->id_cap = std::max<int64_t>(t->cap, 1);
-        if (!tree_alloc(t, m, &t->alive, (size_t)t->id_cap)) r = ZD_ERR_OOM;
+        t->id_words = (std::max<int64_t>(t->cap, 1) + 31) / 32;
+        t->id_cap = 32 * t->id_words;
+        if (!tree_alloc(t, m, &t->alive, (size_t)(2 * t->id_words))) r = ZD_ERR_OOM;
         if (r == ZD_OK) {
-            k_fill_u32<<<grid_for(t->id_cap, 256, 4096), 256, 0, s>>>(t->alive, 0, t->id_cap, 0u);
-            k_fill_u32<<<grid_for(n, 256, 4096), 256, 0, s>>>(t->alive, 0, n, 1u);
+            k_init_bits<<<grid_for(2 * t->id_words, 256, 4096), 256, 0, s>>>(t->alive, t->id_words, n);
             if (cudaGetLastError() != cudaSuccess) r = ZD_ERR_CUDA;
         }
     }
@@ -616,12 +634,13 @@ extern "C" int zd_knn_batched(const zd_tree *t, const void *d_queries, const int
 namespace zdk {
 int update_insert(const TreeView &v, const u64 *keys, const int4 *pts, int64_t n, const void *d_pts,
                   int64_t b, int dim, int B, const uint32_t *shift, int key_bits, int32_t next_id,
-                  u64 *keys_out, int4 *pts_out, u32 *alive, int32_t *d_new_ids, Mem &mem);
-int update_delete_mark(u32 *alive, int64_t id_cap, const int32_t *ids, int64_t b, Mem &mem,
+                  u64 *keys_out, int4 *pts_out, u32 *live, int32_t *d_new_ids, Mem &mem);
+int update_delete_mark(u32 *live, u32 *marked, int64_t id_cap, const int32_t *ids, int64_t b, Mem &mem,
                        int *result);
-int update_delete_unmark(u32 *alive, int64_t id_cap, const int32_t *ids, int64_t b, cudaStream_t s);
-int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *alive, const int32_t *ids,
-                          int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem);
+int update_delete_unmark(u32 *live, u32 *marked, int64_t id_cap, const int32_t *ids, int64_t b, cudaStream_t s);
+int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *live, u32 *marked,
+                          const int32_t *ids, int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem);
+int update_live_bits(u32 *live, int64_t a, int64_t z, int set, cudaStream_t s);
 } // namespace zdk
 
 extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t *d_new_ids, void *stream)
@@ -633,20 +652,21 @@ extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t
     if (t->next_id + b >= ((int64_t)1 << 31) - 2) return ZD_ERR_CAPACITY;
     cudaStream_t s = (cudaStream_t)stream;
     Mem mem = mem_of(t, s);
-    // grow the per-id liveness table if the new ids do not fit
+    // grow the liveness bitmaps if the new ids do not fit
     if (t->next_id + b > t->id_cap) {
-        int64_t nc = std::max<int64_t>(2 * t->id_cap, t->next_id + b);
-        u32 *na = (u32 *)mem.get(sizeof(u32) * (size_t)nc + 16);
+        const int64_t nw = std::max<int64_t>(2 * t->id_words, (t->next_id + b + 31) / 32);
+        const size_t bytes = sizeof(u32) * (size_t)(2 * nw) + 16;
+        u32 *na = (u32 *)mem.get(bytes);
         if (!na) return ZD_ERR_OOM;
-        ZD_CUDA(cudaMemcpyAsync(na, t->alive, sizeof(u32) * t->id_cap, cudaMemcpyDeviceToDevice, s));
-        k_fill_u32<<<grid_for(nc - t->id_cap, 256, 4096), 256, 0, s>>>(na, t->id_cap, nc, 0u);
+        k_grow_bits<<<grid_for(2 * nw, 256, 4096), 256, 0, s>>>(t->alive, t->id_words, na, nw);
         for (int i = 0; i < t->nblocks; ++i)
             if (t->blocks[i].p == t->alive) {
                 mem.put(t->blocks[i].p, t->blocks[i].bytes);
-                t->blocks[i] = Block{na, sizeof(u32) * (size_t)nc + 16};
+                t->blocks[i] = Block{na, bytes};
             }
         t->alive = na;
-        t->id_cap = nc;
+        t->id_words = nw;
+        t->id_cap = 32 * nw;
     }
     // the previous call's device errors must not be mistaken for this one's
     int prior = zd_check(stream);
@@ -657,7 +677,7 @@ extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t
     int st = zd_check(stream);
     if (st != ZD_OK) {
         // nothing was committed: the new ids are released again
-        k_fill_u32<<<grid_for(b, 256, 4096), 256, 0, s>>>(t->alive, t->next_id, t->next_id + b, 0u);
+        update_live_bits(t->alive, t->next_id, t->next_id + b, 0, s);
         return st;
     }
     std::swap(t->keys, t->keys2);
@@ -678,14 +698,14 @@ extern "C" int zd_delete_batch(zd_tree *t, const int32_t *d_ids, int64_t b, void
     int prior = zd_check(stream);
     if (prior != ZD_OK) return prior;
     int result = ZD_OK;
-    ZD_TRY(update_delete_mark(t->alive, t->id_cap, d_ids, b, mem, &result));
+    u32 *live = t->alive, *marked = t->alive + t->id_words;
+    ZD_TRY(update_delete_mark(live, marked, t->id_cap, d_ids, b, mem, &result));
     if (result != ZD_OK) {
-        ZD_TRY(update_delete_unmark(t->alive, t->id_cap, d_ids, b, s));
+        ZD_TRY(update_delete_unmark(live, marked, t->id_cap, d_ids, b, s));
         ZD_CUDA(cudaStreamSynchronize(s));
         return result;
     }
-    if (b > t->n) return ZD_ERR_NOT_FOUND;
-    ZD_TRY(update_delete_compact(t->keys, t->pts, t->n, t->alive, d_ids, b, t->id_cap, t->keys2, t->pts2,
+    ZD_TRY(update_delete_compact(t->keys, t->pts, t->n, live, marked, d_ids, b, t->id_cap, t->keys2, t->pts2,
                                  mem));
     std::swap(t->keys, t->keys2);
     std::swap(t->pts, t->pts2);

@@ -66,12 +66,23 @@ __device__ __forceinline__ int delta_of(u64 a, u64 b) { return a == b ? -1 : 63 
 
 // flag[i] = 1 iff boundary i (between sorted points i and i+1) separates two
 // leaves; block_count[b] = flags in block b's tile.
+//
+// Boundary i's run is bounded by the nearest boundaries on either side with a
+// larger delta.  Both are found by binary lifting over a shared-memory table
+// of window maxima, F_j[e] = max(delta[e .. e + 2^j - 1]): from the
+// neighbour of i outward, skip the largest power-of-two block whose maximum
+// is <= delta_i, for j = J..0, never beyond L - 1 positions.  Every boundary
+// takes the same J + 1 steps per side (no divergent scans).  Positions
+// outside [0, n-1) count as larger than every delta (the ends of the array
+// bound every run).
+constexpr int DELTA_OUT = 1 << 20; // "larger than every delta" (deltas are < 64)
+
 __global__ void __launch_bounds__(FLAG_THREADS) k_split_flags(const u64 *__restrict__ keys, int64_t n,
-                                                              int L, int force_bit,
+                                                              int L, int levels, int force_bit,
                                                               unsigned char *__restrict__ flag,
                                                               int *__restrict__ block_count)
 {
-    __shared__ int s_delta[FLAG_TILE + 2 * MAX_LEAF];
+    extern __shared__ int s_tab[]; // [levels][wn]
     __shared__ int s_cnt[FLAG_THREADS / 32];
     const int64_t nb = n - 1; // number of boundaries
     const int64_t t0 = (int64_t)blockIdx.x * FLAG_TILE;
@@ -79,46 +90,38 @@ __global__ void __launch_bounds__(FLAG_THREADS) k_split_flags(const u64 *__restr
     const int64_t w0 = t0 - L;
     const int wn = FLAG_TILE + 2 * L;
     for (int e = threadIdx.x; e < wn; e += FLAG_THREADS) {
-        int64_t j = w0 + e;
-        s_delta[e] = (j >= 0 && j < nb) ? delta_of(keys[j], keys[j + 1]) : -2;
+        const int64_t j = w0 + e;
+        s_tab[e] = (j >= 0 && j < nb) ? delta_of(keys[j], keys[j + 1]) : DELTA_OUT;
     }
     __syncthreads();
+    for (int lv = 1; lv < levels; ++lv) {
+        const int h = 1 << (lv - 1);
+        const int *prev = s_tab + (lv - 1) * wn;
+        int *cur = s_tab + lv * wn;
+        for (int e = threadIdx.x; e < wn; e += FLAG_THREADS)
+            cur[e] = e + h < wn ? max(prev[e], prev[e + h]) : prev[e];
+        __syncthreads();
+    }
     int cnt = 0;
 #pragma unroll
     for (int it = 0; it < FLAG_ITEMS; ++it) {
         const int e = it * FLAG_THREADS + threadIdx.x;
         const int64_t i = t0 + e;
         if (i >= nb) continue;
-        const int di = s_delta[e + L];
+        const int ei = e + L; // window index of boundary i
+        const int di = s_tab[ei];
         unsigned char f = 0;
         if (di >= 0) {
-            // nearest boundary on the left with a larger delta, within L-1
-            int64_t pg = -1;
-            bool found = false;
-            for (int s = 1; s < L; ++s) {
-                int64_t j = i - s;
-                if (j < 0) break;
-                if (s_delta[e + L - s] > di) {
-                    pg = j;
-                    found = true;
-                    break;
-                }
+            // left: skipped positions ei-1, ei-2, ... whose deltas are <= di
+            int lskip = 0, rskip = 0;
+            for (int lv = levels - 1; lv >= 0; --lv) {
+                const int len = 1 << lv;
+                if (lskip + len <= L - 1 && s_tab[lv * wn + ei - lskip - len] <= di) lskip += len;
+                if (rskip + len <= L - 1 && s_tab[lv * wn + ei + rskip + 1] <= di) rskip += len;
             }
-            if (!found) pg = max(i - L, (int64_t)-1);
-            int64_t ng = nb;
-            found = false;
-            for (int s = 1; s < L; ++s) {
-                int64_t j = i + s;
-                if (j >= nb) break;
-                if (s_delta[e + L + s] > di) {
-                    ng = j;
-                    found = true;
-                    break;
-                }
-            }
-            if (!found) ng = min(i + L, nb);
-            // the run bounded by pg and ng holds ng - pg points; a boundary
-            // between two clouds of a forest always separates leaves
+            // nearest larger at distance lskip + 1 / rskip + 1, or farther than
+            // L - 1 (then the run already holds more than L points)
+            const int64_t pg = i - (lskip + 1), ng = i + (rskip + 1);
             f = (ng - pg > L || di >= force_bit) ? 1 : 0;
         }
         flag[i] = f;
@@ -457,8 +460,13 @@ int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, i
     Scratch<int> bcount(mem, nblocks > 0 ? nblocks : 1);
     if (!flag.p || !bcount.p) return ZD_ERR_OOM;
     if (nblocks > 0) {
-        k_split_flags<<<(unsigned)nblocks, FLAG_THREADS, 0, s>>>(keys, n, leaf_size, force_bit, flag.p,
-                                                                 bcount.p);
+        // table levels: spans 1, 2, 4, ... up to the largest <= L - 1
+        int levels = 1;
+        while ((1 << levels) <= leaf_size - 1) ++levels;
+        const size_t smem = sizeof(int) * (size_t)levels * (FLAG_TILE + 2 * leaf_size);
+        ZD_CUDA(cudaFuncSetAttribute(k_split_flags, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_split_flags<<<(unsigned)nblocks, FLAG_THREADS, smem, s>>>(keys, n, leaf_size, levels, force_bit, flag.p,
+                                                                    bcount.p);
         ZD_CUDA(cudaGetLastError());
     }
     k_scan_counts<<<1, 1024, 0, s>>>(bcount.p, nblocks, n, b.meta, b.leaf_lo);

@@ -75,11 +75,17 @@ __global__ void __launch_bounds__(256) k_merge_new(const u64 *__restrict__ keys,
     }
 }
 
-__global__ void k_set_range_u32(u32 *p, int64_t a, int64_t z, u32 v)
+// Liveness of ids is kept as two bitmaps: live bits in words [0, W) and
+// marked-for-delete bits in words [W, 2W) (W = ceil(id capacity / 32)).  At 4
+// bytes per 32 ids both stay resident in L2 for tens of millions of ids.
+__global__ void k_live_bits(u32 *live, int64_t a, int64_t z, int set)
 {
     for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < z;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = v;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const u32 bit = 1u << (i & 31);
+        if (set) atomicOr(&live[i >> 5], bit);
+        else atomicAnd(&live[i >> 5], ~bit);
+    }
 }
 
 __global__ void k_iota(int32_t *p, int64_t n, int32_t first)
@@ -89,9 +95,17 @@ __global__ void k_iota(int32_t *p, int64_t n, int32_t first)
         p[i] = (int32_t)(first + i);
 }
 
+int update_live_bits(u32 *live, int64_t a, int64_t z, int set, cudaStream_t s)
+{
+    if (z <= a) return ZD_OK;
+    k_live_bits<<<grid_for(z - a, 256, 4096), 256, 0, s>>>(live, a, z, set);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
 int update_insert(const TreeView &v, const u64 *keys, const int4 *pts, int64_t n, const void *d_pts,
                   int64_t b, int dim, int B, const uint32_t *shift, int key_bits, int32_t next_id,
-                  u64 *keys_out, int4 *pts_out, u32 *alive, int32_t *d_new_ids, Mem &mem)
+                  u64 *keys_out, int4 *pts_out, u32 *live, int32_t *d_new_ids, Mem &mem)
 {
     (void)v;
     cudaStream_t s = mem.s;
@@ -111,13 +125,14 @@ int update_insert(const TreeView &v, const u64 *keys, const int4 *pts, int64_t n
         k_merge_old<<<(unsigned)((n + MERGE_TILE - 1) / MERGE_TILE), 256, 0, s>>>(keys, pts, n, bkeys.p, b,
                                                                                keys_out, pts_out);
     k_merge_new<<<grid_for(b, 256, 152 * 16), 256, 0, s>>>(keys, n, bkeys.p, bpts.p, b, keys_out, pts_out);
-    k_set_range_u32<<<grid_for(b, 256, 4096), 256, 0, s>>>(alive, next_id, next_id + b, 1u);
+    k_live_bits<<<grid_for(b, 256, 4096), 256, 0, s>>>(live, next_id, next_id + b, 1);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }
 
 // ----------------------------------------------------------------- delete
-__global__ void k_mark(u32 *alive, int64_t id_cap, const int32_t *__restrict__ ids, int64_t b, int *err)
+__global__ void k_mark(const u32 *live, u32 *marked, int64_t id_cap, const int32_t *__restrict__ ids, int64_t b,
+                       int *err)
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < b;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -126,29 +141,37 @@ __global__ void k_mark(u32 *alive, int64_t id_cap, const int32_t *__restrict__ i
             atomicCAS(err, 0, ZD_ERR_NOT_FOUND);
             continue;
         }
-        const u32 old = atomicCAS(&alive[id], 1u, 2u);
-        if (old == 0u) atomicCAS(err, 0, ZD_ERR_NOT_FOUND);
-        else if (old == 2u) atomicCAS(err, 0, ZD_ERR_DUPLICATE_ID);
+        const u32 bit = 1u << (id & 31);
+        if (!(live[id >> 5] & bit)) {
+            atomicCAS(err, 0, ZD_ERR_NOT_FOUND);
+            continue;
+        }
+        if (atomicOr(&marked[id >> 5], bit) & bit) atomicCAS(err, 0, ZD_ERR_DUPLICATE_ID);
     }
 }
 
-__global__ void k_unmark(u32 *alive, int64_t id_cap, const int32_t *__restrict__ ids, int64_t b, u32 from,
-                         u32 to)
+// Clear the marked bits of the batch's ids (and, with retire, their live bits).
+__global__ void k_unmark(u32 *live, u32 *marked, int64_t id_cap, const int32_t *__restrict__ ids, int64_t b,
+                         int retire)
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < b;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int32_t id = ids[j];
-        if (id >= 0 && id < id_cap && alive[id] == from) alive[id] = to;
+        if (id < 0 || id >= id_cap) continue;
+        const u32 bit = 1u << (id & 31);
+        atomicAnd(&marked[id >> 5], ~bit);
+        if (retire) atomicAnd(&live[id >> 5], ~bit);
     }
 }
 
-int update_delete_mark(u32 *alive, int64_t id_cap, const int32_t *ids, int64_t b, Mem &mem, int *result)
+int update_delete_mark(u32 *live, u32 *marked, int64_t id_cap, const int32_t *ids, int64_t b, Mem &mem,
+                       int *result)
 {
     cudaStream_t s = mem.s;
     Scratch<int> err(mem, 1);
     if (!err.p) return ZD_ERR_OOM;
     ZD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    k_mark<<<grid_for(b, 256, 4096), 256, 0, s>>>(alive, id_cap, ids, b, err.p);
+    k_mark<<<grid_for(b, 256, 4096), 256, 0, s>>>(live, marked, id_cap, ids, b, err.p);
     ZD_CUDA(cudaGetLastError());
     int h = 0;
     ZD_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -157,26 +180,37 @@ int update_delete_mark(u32 *alive, int64_t id_cap, const int32_t *ids, int64_t b
     return ZD_OK;
 }
 
-int update_delete_unmark(u32 *alive, int64_t id_cap, const int32_t *ids, int64_t b, cudaStream_t s)
+int update_delete_unmark(u32 *live, u32 *marked, int64_t id_cap, const int32_t *ids, int64_t b, cudaStream_t s)
 {
-    k_unmark<<<grid_for(b, 256, 4096), 256, 0, s>>>(alive, id_cap, ids, b, 2u, 1u);
+    k_unmark<<<grid_for(b, 256, 4096), 256, 0, s>>>(live, marked, id_cap, ids, b, 0);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }
 
+// Stable compaction of the points whose id is not marked.  Element e of a
+// tile is handled by thread e % 256 in step e / 256, so loads and stores of a
+// warp touch consecutive elements; within a tile, kept elements are ranked in
+// element order with ballots.
 constexpr int CMP_THREADS = 256;
 constexpr int CMP_ITEMS = 8;
 constexpr int CMP_TILE = CMP_THREADS * CMP_ITEMS;
 
-__global__ void __launch_bounds__(CMP_THREADS) k_keep_count(const int4 *__restrict__ pts, int64_t n,
-                                                           const u32 *__restrict__ alive, int *count)
+__global__ void __launch_bounds__(CMP_THREADS) k_keep_flags(const int4 *__restrict__ pts, int64_t n,
+                                                           const u32 *__restrict__ marked,
+                                                           unsigned char *__restrict__ keep, int *count)
 {
     __shared__ int s_w[CMP_THREADS / 32];
     const int64_t t0 = (int64_t)blockIdx.x * CMP_TILE;
     int c = 0;
+#pragma unroll
     for (int it = 0; it < CMP_ITEMS; ++it) {
-        int64_t i = t0 + it * CMP_THREADS + threadIdx.x;
-        if (i < n) c += alive[pts[i].w] != 2u;
+        const int64_t i = t0 + it * CMP_THREADS + threadIdx.x;
+        if (i < n) {
+            const int id = pts[i].w;
+            const unsigned char k = (marked[id >> 5] >> (id & 31)) & 1u ? 0 : 1;
+            keep[i] = k;
+            c += k;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
@@ -223,57 +257,64 @@ __global__ void __launch_bounds__(1024) k_excl_scan(int *count, int64_t nb)
     }
 }
 
-// Stable scatter of the kept points: thread-blocked so the order survives.
 __global__ void __launch_bounds__(CMP_THREADS) k_keep_scatter(const u64 *__restrict__ keys,
                                                              const int4 *__restrict__ pts, int64_t n,
-                                                             const u32 *__restrict__ alive,
+                                                             const unsigned char *__restrict__ keep,
                                                              const int *__restrict__ off,
                                                              u64 *__restrict__ keys_out,
                                                              int4 *__restrict__ pts_out)
 {
-    __shared__ int s_w[CMP_THREADS / 32];
-    const int64_t t0 = (int64_t)blockIdx.x * CMP_TILE + (int64_t)threadIdx.x * CMP_ITEMS;
+    __shared__ int s_cnt[CMP_ITEMS][CMP_THREADS / 32];
+    const int64_t t0 = (int64_t)blockIdx.x * CMP_TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    bool keep[CMP_ITEMS];
-    int c = 0;
+    unsigned ball[CMP_ITEMS];
 #pragma unroll
     for (int it = 0; it < CMP_ITEMS; ++it) {
-        int64_t i = t0 + it;
-        keep[it] = i < n && alive[pts[i].w] != 2u;
-        c += keep[it];
+        const int64_t i = t0 + it * CMP_THREADS + threadIdx.x;
+        ball[it] = __ballot_sync(0xffffffffu, i < n && keep[i]);
+        if (lane == 0) s_cnt[it][warp] = __popc(ball[it]);
     }
-    int x = c;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
     __syncthreads();
-    int wo = 0;
-    for (int w = 0; w < warp; ++w) wo += s_w[w];
-    int64_t pos = off[blockIdx.x] + wo + x - c;
-#pragma unroll
-    for (int it = 0; it < CMP_ITEMS; ++it)
-        if (keep[it]) {
-            keys_out[pos] = keys[t0 + it];
-            pts_out[pos] = pts[t0 + it];
-            ++pos;
+    // element order within the tile is (it, warp, lane): exclusive scan of the
+    // (it, warp) counts in that order
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int q = 0; q < CMP_ITEMS * (CMP_THREADS / 32); ++q) {
+            int &cq = s_cnt[q / (CMP_THREADS / 32)][q % (CMP_THREADS / 32)];
+            const int c = cq;
+            cq = run;
+            run += c;
         }
+    }
+    __syncthreads();
+    const int base = off[blockIdx.x];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int it = 0; it < CMP_ITEMS; ++it) {
+        const int before = s_cnt[it][warp];
+        if (ball[it] & (1u << lane)) {
+            const int64_t i = t0 + it * CMP_THREADS + threadIdx.x;
+            const int64_t pos = base + before + __popc(ball[it] & lt);
+            keys_out[pos] = keys[i];
+            pts_out[pos] = pts[i];
+        }
+    }
 }
 
-int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *alive, const int32_t *ids,
-                          int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem)
+int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *live, u32 *marked,
+                          const int32_t *ids, int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem)
 {
     cudaStream_t s = mem.s;
     const int64_t nb = (n + CMP_TILE - 1) / CMP_TILE;
     Scratch<int> count(mem, nb > 0 ? nb : 1);
-    if (!count.p) return ZD_ERR_OOM;
+    Scratch<unsigned char> keep(mem, n > 0 ? n : 1);
+    if (!count.p || !keep.p) return ZD_ERR_OOM;
     if (nb > 0) {
-        k_keep_count<<<(unsigned)nb, CMP_THREADS, 0, s>>>(pts, n, alive, count.p);
+        k_keep_flags<<<(unsigned)nb, CMP_THREADS, 0, s>>>(pts, n, marked, keep.p, count.p);
         k_excl_scan<<<1, 1024, 0, s>>>(count.p, nb);
-        k_keep_scatter<<<(unsigned)nb, CMP_THREADS, 0, s>>>(keys, pts, n, alive, count.p, keys_out, pts_out);
+        k_keep_scatter<<<(unsigned)nb, CMP_THREADS, 0, s>>>(keys, pts, n, keep.p, count.p, keys_out, pts_out);
     }
-    k_unmark<<<grid_for(b, 256, 4096), 256, 0, s>>>(alive, id_cap, ids, b, 2u, 0u);
+    k_unmark<<<grid_for(b, 256, 4096), 256, 0, s>>>(live, marked, id_cap, ids, b, 1);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }
