@@ -266,9 +266,10 @@ def run_ours(args):
     achieved = kb / (knn_avg / 1e3) / 1e9
     traffic = profiled_traffic("k_knn_group", "3d-clustered-1e7") if n == 10_000_000 else None
     bb = build_bytes_per_point() * n
-    # build: 2 id-table fills, encode, plan, 8 sort passes, finish, gather,
-    # split flags, scan, leaf index, internal nodes, boxes, float copy (20);
-    # k-NN: warp groups + exact fallback (2)
+    # build: liveness bitmap init, encode, plan, 8 sort passes, finish,
+    # gather, split flags, scan, leaf index, internal nodes,
+    # boxes, float copy (20); k-NN: warp groups + exact
+    # fallback (2)
     launches_per_step = 22
     out = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,

@@ -412,7 +412,9 @@ int zd_build_batched(const zd_params *p, const zd_allocator *alloc, const void *
     for (int64_t c = 0; c < n_clouds; ++c) t->n_groups += (h_offsets[c + 1] - h_offsets[c] + 31) / 32;
     if (r == ZD_OK && !tree_alloc(t, m, &t->group_start, (size_t)std::max<int64_t>(t->n_groups, 1)))
         r = ZD_ERR_OOM;
-    if (r == ZD_OK) r = launch_group_starts(t->cloud_off, n_clouds, t->n_groups, t->group_start, m);
+    Scratch<int64_t> gpre(m, (size_t)n_clouds + 1);
+    if (r == ZD_OK && !gpre.p) r = ZD_ERR_OOM;
+    if (r == ZD_OK) r = launch_group_starts(t->cloud_off, n_clouds, t->n_groups, t->group_start, gpre.p, s);
     if (r != ZD_OK) {
         tree_release(t, s);
         free(t);
@@ -550,7 +552,7 @@ static int prepare_queries(const zd_tree *t, const void *d_q, int64_t m, const i
 }
 
 static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m, int k, int mode,
-                   int32_t *d_idx, void *d_dist, cudaStream_t s)
+                   int32_t *d_idx, void *d_dist, cudaStream_t s, const int64_t *d_qoff = nullptr)
 {
     const int variant = mode & (ZD_KNN_THREAD_PER_QUERY | ZD_KNN_WARP_GROUP);
     mode &= 0xff;
@@ -566,16 +568,33 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
     a.out_idx = d_idx;
     a.out_dist = d_dist;
     a.shift = make_uint3(t->p.shift[0], t->p.shift[1], t->p.shift[2]);
-    // warp groups: integer trees, all points or bit-based external queries
-    const bool group = !t->is_float && variant != ZD_KNN_THREAD_PER_QUERY &&
-                       (mode == ZD_SEARCH_LEAF || (mode == ZD_SEARCH_BIT && !t->cloud_off));
+    // warp groups: all points, bit-based external queries, and external
+    // queries of a forest (grouped per query cloud)
+    const bool forest_ext = t->cloud_off && d_qoff;
+    const bool group = variant != ZD_KNN_THREAD_PER_QUERY &&
+                       (mode == ZD_SEARCH_LEAF || (mode == ZD_SEARCH_BIT && !t->cloud_off) || forest_ext);
     if (!group) return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s);
+    if (forest_ext) a.mode = ZD_SEARCH_BIT;
+    const bool allpts = mode == ZD_SEARCH_LEAF;
+    Mem mem = mem_of(t, s);
+    Scratch<int64_t> gpre(mem, forest_ext ? (size_t)t->n_clouds + 1 : 1);
+    Scratch<int> qstart(mem, forest_ext ? (size_t)((m + 31) / 32 + t->n_clouds) : 1);
+    if (!gpre.p || !qstart.p) return ZD_ERR_OOM;
+    if (allpts) {
+        a.group_start = t->group_start;
+        a.n_groups = t->cloud_off ? t->n_groups : (t->n + 31) / 32;
+    } else if (forest_ext) {
+        a.n_groups = (m + 31) / 32 + t->n_clouds;
+        ZD_TRY(launch_group_starts(d_qoff, t->n_clouds, a.n_groups, qstart.p, gpre.p, s));
+        a.group_start = qstart.p;
+        a.group_count = gpre.p + t->n_clouds;
+        a.q_off = d_qoff;
+    } else {
+        a.n_groups = (m + 31) / 32;
+    }
+    if (t->is_float) return launch_knn_group_f32(a, s);
     // packed keys: the ids need idb bits
     a.idb = std::max(1, ceil_log2(t->cloud_off ? t->max_cloud : t->next_id));
-    const bool allpts = mode == ZD_SEARCH_LEAF;
-    a.group_start = allpts ? t->group_start : nullptr;
-    a.n_groups = allpts ? (t->cloud_off ? t->n_groups : (t->n + 31) / 32) : (m + 31) / 32;
-    Mem mem = mem_of(t, s);
     Scratch<int> fix(mem, (size_t)(allpts ? t->n : m) + 1);
     if (!fix.p) return ZD_ERR_OOM;
     a.fix_count = fix.p;
@@ -626,7 +645,7 @@ extern "C" int zd_knn_batched(const zd_tree *t, const void *d_queries, const int
     Scratch<int4> q4(mem, m);
     if (!qkeys.p || !q4.p) return ZD_ERR_OOM;
     ZD_TRY(prepare_queries(t, d_queries, m, d_query_offsets, t->n_clouds, mem, qkeys.p, q4.p));
-    ZD_TRY(run_knn(t, q4.p, qkeys.p, m, k, ZD_SEARCH_ROOT, d_idx, d_dist, s));
+    ZD_TRY(run_knn(t, q4.p, qkeys.p, m, k, ZD_SEARCH_ROOT | mode_flags, d_idx, d_dist, s, d_query_offsets));
     return mem.failed ? ZD_ERR_OOM : ZD_OK;
 }
 

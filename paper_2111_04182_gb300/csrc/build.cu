@@ -431,18 +431,16 @@ __global__ void k_group_starts(const int64_t *__restrict__ off, const int64_t *_
             if (gpre[mid] <= g) a = mid;
             else z = mid - 1;
         }
-        start[g] = (int)(off[a] + 32 * (g - gpre[a]));
+        if (g < gpre[nc]) start[g] = (int)(off[a] + 32 * (g - gpre[a]));
     }
 }
 
 int launch_group_starts(const int64_t *cloud_off, int64_t n_clouds, int64_t n_groups, int *group_start,
-                        Mem &mem)
+                        int64_t *gpre, cudaStream_t s)
 {
-    if (n_groups <= 0) return ZD_OK;
-    Scratch<int64_t> gpre(mem, n_clouds + 1);
-    if (!gpre.p) return ZD_ERR_OOM;
-    k_group_prefix<<<1, 1024, 0, mem.s>>>(cloud_off, n_clouds, gpre.p);
-    k_group_starts<<<grid_for(n_groups, 256, 152 * 16), 256, 0, mem.s>>>(cloud_off, gpre.p, n_clouds, n_groups,
+    k_group_prefix<<<1, 1024, 0, s>>>(cloud_off, n_clouds, gpre);
+    if (n_groups > 0)
+        k_group_starts<<<grid_for(n_groups, 256, 152 * 16), 256, 0, s>>>(cloud_off, gpre, n_clouds, n_groups,
                                                                         group_start);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;

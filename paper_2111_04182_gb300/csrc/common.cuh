@@ -176,8 +176,10 @@ int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, i
 
 // Forests: group_start[g] = first sorted position of the g-th 32-point group,
 // groups laid out cloud by cloud so that none crosses a cloud boundary.
+// gpre: device scratch [n_clouds + 1] owned by the caller; gpre[n_clouds]
+// receives the number of groups (n_groups only bounds the launch).
 int launch_group_starts(const int64_t *cloud_off, int64_t n_clouds, int64_t n_groups, int *group_start,
-                        Mem &mem);
+                        int64_t *gpre, cudaStream_t s);
 
 // -------------------------------------------------------------------- knn
 struct KnnArgs {
@@ -195,7 +197,9 @@ struct KnnArgs {
     // warp-group mapping (integer coordinates)
     int idb;                 // id bits of the packed (d^2, id) keys
     const int *group_start;  // first sorted position of every group (forests), or null
-    int64_t n_groups;
+    int64_t n_groups;        // groups launched (an upper bound when group_count is set)
+    const int64_t *group_count; // device: groups that exist, or null
+    const int64_t *q_off;    // forests, external queries: device query offsets [n_clouds + 1]
     int *fix_list;           // queries whose packed k-th distance saturated
     int *fix_count;
     // exact kernel restricted to listed sorted positions (fallback), or null
@@ -205,6 +209,7 @@ struct KnnArgs {
 int launch_knn_i32(const KnnArgs &a, cudaStream_t s);
 int launch_knn_group_i32(const KnnArgs &a, cudaStream_t s); // + exact fallback
 int launch_knn_f32(const KnnArgs &a, cudaStream_t s);
+int launch_knn_group_f32(const KnnArgs &a, cudaStream_t s);
 
 // --------------------------------------------------------------- backward
 int launch_backward(const float *q, const float *ref, const int32_t *idx, int64_t batch, int64_t m,

@@ -285,6 +285,13 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
         l0 = __reduce_min_sync(0xffffffffu, c.live ? mine : INT_MAX);
         l1 = __reduce_max_sync(0xffffffffu, c.live ? mine : -1);
     }
+    if (t.cloud_off && !allpts) {
+        // the bit descent reaches the query's own cloud iff that cloud has points
+        const u64 cloud = __shfl_sync(0xffffffffu, c.qkey, 0) >> t.cloud_bit;
+        if ((__ldg(t.keys + __ldg(t.leaf_lo + l0)) >> t.cloud_bit) != cloud ||
+            (__ldg(t.keys + __ldg(t.leaf_lo + l1)) >> t.cloud_bit) != cloud)
+            return;
+    }
     const int P0 = __ldg(t.leaf_lo + l0), P1 = __ldg(t.leaf_lo + l1 + 1);
     if (FS) group_scan_f<DIM, K>(t, P0, P1, c, key, thr, thr_f);
     else group_scan<DIM, K>(t, P0, P1, c, key, thr);
@@ -337,15 +344,16 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
     int *stack = s_stack[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int64_t g = ((int64_t)blockIdx.x * KNN_THREADS + threadIdx.x) >> 5;
-    if (g >= a.n_groups) return; // whole warp
+    if (g >= a.n_groups || (a.group_count && g >= *a.group_count)) return; // whole warp
     const bool allpts = a.mode == ZD_SEARCH_LEAF;
     const int64_t nq = allpts ? t.n : a.m;
     // the group: 32 consecutive queries in Morton order, never across clouds
     const int g0 = a.group_start ? __ldg(a.group_start + g) : (int)(g * 32);
     int gend = (int)min((int64_t)g0 + 32, nq);
-    if (t.cloud_off && allpts) {
-        const int64_t ce = __ldg(t.cloud_off + (__ldg(t.keys + g0) >> t.cloud_bit) + 1);
-        gend = (int)min((int64_t)gend, ce);
+    if (t.cloud_off) {
+        const u64 key0 = allpts ? __ldg(t.keys + g0) : __ldg(a.qkey + g0);
+        const int64_t *off = allpts ? t.cloud_off : a.q_off;
+        gend = (int)min((int64_t)gend, __ldg(off + (key0 >> t.cloud_bit) + 1));
     }
     const int qi = g0 + lane;
     GroupCtx c;

@@ -16,6 +16,9 @@ int launch_knn_group_i32(const KnnArgs &a, cudaStream_t s)
     KnnArgs f = a;
     f.sel = a.fix_list;
     f.sel_count = a.fix_count;
+    // forest external queries fall back to the root-based search, which
+    // descends to the query's own cloud first
+    if (a.t.cloud_off && a.mode == ZD_SEARCH_BIT) f.mode = ZD_SEARCH_ROOT;
     return launch_knn_i32(f, s);
 }
 } // namespace zdk

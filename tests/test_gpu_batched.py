@@ -79,7 +79,8 @@ def test_batched_all_points_per_cloud(zd, oracle, mapping):
     t.free()
 
 
-def test_batched_external_float_queries(zd, oracle):
+@pytest.mark.parametrize("mapping", [0x100, 0x200])
+def test_batched_external_float_queries(zd, oracle, mapping):
     from paper_2111_04182_gb300 import datagen
     rng = np.random.default_rng(12)
     P = 5
@@ -88,7 +89,7 @@ def test_batched_external_float_queries(zd, oracle):
     offB = np.concatenate([[0], np.cumsum([len(b) for b in B])])
     t = zd.zd_build_batched(torch.from_numpy(np.concatenate(B)).to(DEV), offB, 8, 21)
     idx, dist = zd.zd_knn_batched(t, 8, queries=torch.from_numpy(np.concatenate(A)).to(DEV),
-                                  query_offsets=offA)
+                                  query_offsets=offA, mapping=mapping)
     assert zd.zd_check() == 0
     idx = idx.cpu().numpy()
     for p in range(P):
@@ -140,3 +141,31 @@ def test_batched_step_in_cuda_graph_matches_eager(zd, oracle):
     a, z = int(off[c]), int(off[c + 1])
     bi, bd = oracle.knn_brute(w["pts"][a:z], 16)
     assert np.array_equal(ref_i[a:z].cpu().numpy(), bi)
+
+
+@pytest.mark.parametrize("mapping", [0x100, 0x200])
+def test_batched_external_int_queries(zd, oracle, mapping):
+    """External integer queries per cloud, including an empty cloud and a
+    cloud with no queries."""
+    rng = np.random.default_rng(21)
+    sizes = [500, 0, 1200, 37, 900]
+    qsizes = [300, 50, 0, 400, 260]
+    B = [rng.integers(0, 2 ** 16, size=(s, 3)).astype(np.int32) for s in sizes]
+    A = [rng.integers(0, 2 ** 16, size=(s, 3)).astype(np.int32) for s in qsizes]
+    offB = np.concatenate([[0], np.cumsum(sizes)])
+    offA = np.concatenate([[0], np.cumsum(qsizes)])
+    t = zd.zd_build_batched(torch.from_numpy(np.concatenate(B)).to(DEV), offB, 8, 16)
+    idx, d2 = zd.zd_knn_batched(t, 6, queries=torch.from_numpy(np.concatenate(A)).to(DEV),
+                                query_offsets=offA, mapping=mapping)
+    assert zd.zd_check() == 0
+    idx, d2 = idx.cpu().numpy(), d2.cpu().numpy()
+    for c in range(5):
+        a, z = offA[c], offA[c + 1]
+        if z == a:
+            continue
+        if sizes[c] == 0:
+            assert np.all(idx[a:z] == -1)
+            continue
+        bi, bd = oracle.knn_brute(B[c], 6, queries=A[c])
+        assert np.array_equal(idx[a:z], bi) and np.array_equal(d2[a:z], bd), c
+    t.free()

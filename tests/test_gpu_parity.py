@@ -220,7 +220,8 @@ def test_knn_2d_uniform_workload(zd, oracle):
 
 
 # --------------------------------------------------------------- float
-def test_float_knn_fp64_ranking(zd, oracle):
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_float_knn_fp64_ranking(zd, oracle, mapping):
     from paper_2111_04182_gb300 import datagen
     rng = np.random.default_rng(77)
     a, b = datagen.warped_pair(rng, 6000, 12000)
@@ -232,11 +233,11 @@ def test_float_knn_fp64_ranking(zd, oracle):
     assert np.array_equal(e["keys"], o["keys"]), "float quantization / keys"
     assert np.array_equal(canonical(e)["bit"], o["bit"])
     for mode in (1, 2):
-        idx, dist = t.knn(8, queries=_t(a), mode=mode)
+        idx, dist = t.knn(8, queries=_t(a), mode=mode, mapping=mapping)
         bi, bd = oracle.knn_brute(b, 8, queries=a)
         assert np.array_equal(idx.cpu().numpy(), bi)
         assert np.allclose(dist.cpu().numpy(), np.sqrt(bd), rtol=1e-6, atol=0)
-    idx, dist = t.knn(6)
+    idx, dist = t.knn(6, mapping=mapping)
     bi, bd = oracle.knn_brute(b, 6)
     assert np.array_equal(idx.cpu().numpy(), bi)
     t.free()
