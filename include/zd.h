@@ -64,11 +64,13 @@ enum { ZD_COORD_I32 = 0, ZD_COORD_F32 = 1 };
 enum { ZD_SEARCH_LEAF = 0, ZD_SEARCH_BIT = 1, ZD_SEARCH_ROOT = 2 };
 
 /* Optional thread mapping of a search, OR-ed into the mode of zd_knn /
- * zd_knn_batched (default: the library's choice).  ZD_KNN_THREAD_PER_QUERY:
- * one thread runs one query's traversal.  ZD_KNN_WARP_GROUP (leaf-based mode,
- * integer trees): one warp runs one shared traversal for 32 consecutive
- * points in Morton order, each lane keeping its own k best.  Both return the
- * same exact neighbours. */
+ * zd_knn_batched.  ZD_KNN_THREAD_PER_QUERY: one thread runs one query's
+ * traversal.  ZD_KNN_WARP_GROUP (leaf- and bit-based modes, and external
+ * queries of a forest): one warp runs one shared traversal for 32 queries
+ * that are consecutive in Morton order, each lane keeping its own k best.
+ * Both return the same exact neighbours.  Default (neither flag): warp groups
+ * for all points and for external queries at least a quarter as many as the
+ * tree's points, one thread per query for sparser queries. */
 enum { ZD_KNN_THREAD_PER_QUERY = 0x100, ZD_KNN_WARP_GROUP = 0x200 };
 
 /* Largest k of one search (neighbour lists are register-resident). */
