@@ -57,12 +57,18 @@ __device__ __forceinline__ int64_t segment_of(const int64_t *seg_off, int64_t n_
     return a;
 }
 
-// Warp-aggregated digit histogram update: lanes holding the same digit add
-// once.  All 32 lanes must call it (valid = false for padding lanes).
+// Digit histogram update.  The top digits repeat across neighbouring input
+// points (a spatially coherent input shares its high Morton bits), so lanes
+// holding the same top digit add once (match_any); the low digits are close
+// to random and take plain shared-memory atomics.  All 32 lanes must call it
+// (valid = false for padding lanes).
 __device__ __forceinline__ void hist_add(u32 *sh, u64 key, bool valid, int npasses)
 {
     const unsigned lane = threadIdx.x & 31;
-    for (int p = 0; p < npasses; ++p) {
+    const int top = npasses > 3 ? npasses - 3 : 0;
+    if (valid)
+        for (int p = 0; p < top; ++p) atomicAdd(&sh[p * RADIX + (int)((key >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
+    for (int p = top; p < npasses; ++p) {
         int d = valid ? (int)((key >> (RADIX_BITS * p)) & (RADIX - 1)) : RADIX;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         if (d < RADIX && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh[p * RADIX + d], __popc(peers));
