@@ -272,10 +272,9 @@ def run_ours(args):
     traffic = profiled_traffic("k_knn_group", "3d-clustered-1e7") if n == 10_000_000 else None
     bb = build_bytes_per_point() * n
     # build: liveness bitmap init, encode, plan, 8 sort passes, finish,
-    # gather, split flags, scan, leaf index, internal nodes,
-    # boxes, float copy (20); k-NN: warp groups + exact
-    # fallback (2)
-    launches_per_step = 22
+    # gather, split flags, scan, leaf index, internal nodes, boxes, float
+    # copy (19); k-NN: warp groups + exact fallback (2)
+    launches_per_step = 21
     out = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
