@@ -51,7 +51,7 @@ typedef enum zd_status {
     ZD_ERR_NOT_FOUND = 5,    /* delete of an id that is not live */
     ZD_ERR_DUPLICATE_ID = 6, /* the same id twice in one delete batch */
     ZD_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
-    ZD_ERR_UNIMPLEMENTED = 8,/* a parameter combination not built (e.g. k > 32) */
+    ZD_ERR_UNIMPLEMENTED = 8,/* a parameter combination not built (e.g. k > ZD_MAX_K) */
     ZD_ERR_CAPACITY = 9      /* an insert beyond the tree's capacity */
 } zd_status;
 
@@ -73,8 +73,18 @@ enum { ZD_SEARCH_LEAF = 0, ZD_SEARCH_BIT = 1, ZD_SEARCH_ROOT = 2 };
  * tree's points, one thread per query for sparser queries. */
 enum { ZD_KNN_THREAD_PER_QUERY = 0x100, ZD_KNN_WARP_GROUP = 0x200 };
 
-/* Largest k of one search (neighbour lists are register-resident). */
-#define ZD_MAX_K 32
+/* OR-ed into ZD_SEARCH_BIT or ZD_SEARCH_ROOT with d_queries NULL: the k-NN
+ * graph of the tree's own points (each excluding itself), every query started
+ * the bit-based or root-based way -- the paper's three ways of computing the
+ * k-NN graph (Sec. 2, Sec. 5).  The answer is the same for all three; these
+ * starts always run one thread (or, for k > 32, one warp) per query. */
+enum { ZD_KNN_ALL_POINTS = 0x400 };
+
+/* Largest k of one search.  Up to 32 neighbours a query's list lives in one
+ * thread's registers (both mappings above); for 32 < k <= ZD_MAX_K one warp
+ * serves one query with the list spread over its lanes, whatever the mapping
+ * flags say. */
+#define ZD_MAX_K 128
 
 typedef struct zd_params {
     int32_t dim;        /* 2 or 3 */
@@ -197,10 +207,10 @@ int zd_export_tree(const zd_tree *t, int32_t *d_ids, uint64_t *d_keys, int32_t *
 /* Exact k-NN (Algorithms 2 and 3).  Neighbours are ranked by (squared
  * distance, id): int64 exact for integer trees, fp64 evaluated as
  * ((dx*dx + dy*dy) + dz*dz) without contraction for float trees.
- *   mode ZD_SEARCH_LEAF: d_queries must be NULL; every live point is a query
- *     and excludes itself (by id); row r of the outputs is the point with id
- *     r, so the outputs need next_id rows (rows of deleted ids are left
- *     untouched).
+ *   mode ZD_SEARCH_LEAF (or ZD_SEARCH_BIT / ZD_SEARCH_ROOT | ZD_KNN_ALL_POINTS):
+ *     d_queries must be NULL; every live point is a query and excludes itself
+ *     (by id); row r of the outputs is the point with id r, so the outputs
+ *     need next_id rows (rows of deleted ids are left untouched).
  *   mode ZD_SEARCH_BIT / ZD_SEARCH_ROOT: d_queries [m, dim] (the tree's
  *     coordinate type) are external queries; row r is query r.  The queries
  *     are sorted by Morton key first (Sec. 3.1), so bit-based queries must
@@ -208,7 +218,7 @@ int zd_export_tree(const zd_tree *t, int32_t *d_ids, uint64_t *d_keys, int32_t *
  * d_idx [rows, k] gets ids (-1 where fewer than k candidates exist); d_dist
  * [rows, k] (may be NULL) gets int64 squared distances (integer trees,
  * INT64_MAX padding) or float32 Euclidean distances computed in fp32 (float
- * trees, +inf padding).  1 <= k <= ZD_MAX_K. */
+ * trees, +inf padding).  1 <= k <= ZD_MAX_K (larger k: ZD_ERR_UNIMPLEMENTED). */
 int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k, int mode, int32_t *d_idx,
            void *d_dist, void *stream);
 

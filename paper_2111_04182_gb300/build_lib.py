@@ -13,7 +13,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_lib", "libzd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["sort.cu", "build.cu", "knn_i32.cu", "knn_f32.cu", "update.cu", "backward.cu", "api.cu"]
+SOURCES = ["sort.cu", "build.cu", "knn_i32.cu", "knn_f32.cu", "knn_wide.cu", "update.cu", "backward.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -561,6 +561,7 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
     a.t = view_of(t);
     a.k = k;
     a.mode = mode;
+    a.allpts = q4 == nullptr;
     a.is_float = t->is_float;
     a.q = q4;
     a.qkey = qkeys;
@@ -576,12 +577,17 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
     // apart in a group, whose shared traversal then covers much more than
     // each query needs, and one thread per query is faster (measured: 10^6
     // queries into 5*10^7 points 2.9 vs 5.5 ms; 10^7 into 10^7 13.1 vs 11.1).
-    const bool dense = mode == ZD_SEARCH_LEAF || 4 * m >= t->n;
+    if (k > KNN_MAX_K_REG) return launch_knn_wide(a, s);
+    // Warp groups serve leaf-based all points and bit-based external queries;
+    // all points started from the root or by key bits run one thread per
+    // query (Algorithms 2 / 3 as the paper states them).
+    const bool allpts = a.allpts;
+    const bool dense = allpts || 4 * m >= t->n;
     const bool group = (variant == ZD_KNN_WARP_GROUP || (variant == 0 && dense)) &&
-                       (mode == ZD_SEARCH_LEAF || (mode == ZD_SEARCH_BIT && !t->cloud_off) || forest_ext);
+                       (allpts ? mode == ZD_SEARCH_LEAF
+                               : ((mode == ZD_SEARCH_BIT && !t->cloud_off) || forest_ext));
     if (!group) return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s);
     if (forest_ext) a.mode = ZD_SEARCH_BIT;
-    const bool allpts = mode == ZD_SEARCH_LEAF;
     Mem mem = mem_of(t, s);
     Scratch<int64_t> gpre(mem, forest_ext ? (size_t)t->n_clouds + 1 : 1);
     Scratch<int> qstart(mem, forest_ext ? (size_t)((m + 31) / 32 + t->n_clouds) : 1);
@@ -615,14 +621,15 @@ extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k,
     if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
     if (t->cloud_off) return ZD_ERR_INVALID_ARG; // forests: zd_knn_batched
     cudaStream_t s = (cudaStream_t)stream;
-    const int flags = mode & ~0xff;
+    const int flags = mode & ~0xff & ~ZD_KNN_ALL_POINTS;
     if (flags & ~(ZD_KNN_THREAD_PER_QUERY | ZD_KNN_WARP_GROUP)) return ZD_ERR_INVALID_ARG;
-    if ((mode & 0xff) == ZD_SEARCH_LEAF) {
+    const int base = mode & 0xff;
+    if (base != ZD_SEARCH_LEAF && base != ZD_SEARCH_BIT && base != ZD_SEARCH_ROOT) return ZD_ERR_INVALID_ARG;
+    if (base == ZD_SEARCH_LEAF || (mode & ZD_KNN_ALL_POINTS)) {
         if (d_queries) return ZD_ERR_INVALID_ARG;
-        return run_knn(t, nullptr, nullptr, t->n, k, mode, d_idx, d_dist, s);
+        return run_knn(t, nullptr, nullptr, t->n, k, base | flags, d_idx, d_dist, s);
     }
-    mode &= 0xff;
-    if (mode != ZD_SEARCH_BIT && mode != ZD_SEARCH_ROOT) return ZD_ERR_INVALID_ARG;
+    mode = base;
     if (m < 0 || m >= ((int64_t)1 << 31) - 2 || (m > 0 && !d_queries)) return ZD_ERR_INVALID_ARG;
     if (m == 0) return ZD_OK;
     Mem mem = mem_of(t, s);

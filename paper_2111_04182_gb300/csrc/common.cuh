@@ -182,10 +182,13 @@ int launch_group_starts(const int64_t *cloud_off, int64_t n_clouds, int64_t n_gr
                         int64_t *gpre, cudaStream_t s);
 
 // -------------------------------------------------------------------- knn
+constexpr int KNN_MAX_K_REG = 32; // largest k kept in one thread's registers
+
 struct KnnArgs {
     TreeView t;
     int k;
-    int mode;              // ZD_SEARCH_*
+    int mode;              // ZD_SEARCH_*: how a query finds its start
+    int allpts;            // queries are the tree's own points (self excluded)
     int is_float;
     // external queries, already in Morton order
     const int4 *q;         // (x, y, z, row) in tree coordinates (float bits for float trees)
@@ -210,6 +213,9 @@ int launch_knn_i32(const KnnArgs &a, cudaStream_t s);
 int launch_knn_group_i32(const KnnArgs &a, cudaStream_t s); // + exact fallback
 int launch_knn_f32(const KnnArgs &a, cudaStream_t s);
 int launch_knn_group_f32(const KnnArgs &a, cudaStream_t s);
+// Large k (KNN_MAX_K_REG < k <= ZD_MAX_K): one warp per query, any mode and
+// mapping, integer or float.
+int launch_knn_wide(const KnnArgs &a, cudaStream_t s);
 
 // --------------------------------------------------------------- backward
 int launch_backward(const float *q, const float *ref, const int32_t *idx, int64_t batch, int64_t m,

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
     const int lane = threadIdx.x & 31;
     const int64_t g = ((int64_t)blockIdx.x * KNN_THREADS + threadIdx.x) >> 5;
     if (g >= a.n_groups || (a.group_count && g >= *a.group_count)) return; // whole warp
-    const bool allpts = a.mode == ZD_SEARCH_LEAF;
+    const bool allpts = a.allpts;
     const int64_t nq = allpts ? t.n : a.m;
     // the group: 32 consecutive queries in Morton order, never across clouds
     const int g0 = a.group_start ? __ldg(a.group_start + g) : (int)(g * 32);

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group_f(KnnArgs a, u32 *sta
     int *stack = s_stack[threadIdx.x >> 5];
     const int64_t g = ((int64_t)blockIdx.x * KNN_THREADS + threadIdx.x) >> 5;
     if (g >= a.n_groups || (a.group_count && g >= *a.group_count)) return; // whole warp
-    const bool allpts = a.mode == ZD_SEARCH_LEAF;
+    const bool allpts = a.allpts;
     const int64_t nq = allpts ? t.n : a.m;
     const int g0 = a.group_start ? __ldg(a.group_start + g) : (int)(g * 32);
     int gend = (int)min((int64_t)g0 + 32, nq);

@@ -6,10 +6,14 @@
 // registers, sorted by (squared distance, id) -- the total order that makes
 // ties have one answer -- and walks the tree with an explicit stack:
 //
-//   leaf-based / bit-based (Algorithm 3): scan the start leaf, then climb;
-//     at each ancestor, stop once no point outside the current node's box can
-//     be within the k-th distance, else search the sibling downwards.
+//   leaf-based / bit-based (Algorithm 3): scan the start leaf (all points:
+//     the point's own leaf, or the leaf its key bits lead to from the root;
+//     external queries: the leaf their key bits lead to), then climb; at each
+//     ancestor, stop once no point outside the current node's box can be
+//     within the k-th distance, else search the sibling downwards.
 //   root-based (Algorithm 2): search down from the root.
+// For all points (a.allpts) the queries are the tree's own points in sorted
+// order and each excludes itself, whichever of the three starts is used.
 //
 // searchDown visits a node iff its box distance^2 <= the current k-th
 // distance^2 (non-strict, so an equal distance with a smaller id is never
@@ -282,7 +286,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
     int4 qp;
     int self = -1;
     int64_t row;
-    if (a.mode == ZD_SEARCH_LEAF) {
+    if (a.allpts) {
         qp = __ldg(t.pts + qi);
         self = (int)qi;
         row = qp.w;
@@ -292,6 +296,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
         row = qp.w;
     }
     const typename M::Q q = M::make(qp);
+    const u64 *qkeys = a.allpts ? t.keys : a.qkey;
 
     if (t.n > 0) {
         if (a.mode == ZD_SEARCH_ROOT) {
@@ -299,7 +304,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
             bool ok = true;
             if (t.cloud_off) {
                 // descend to the root of the query's own cloud
-                const u64 cloud = __ldg(a.qkey + qi) >> t.cloud_bit;
+                const u64 cloud = __ldg(qkeys + qi) >> t.cloud_bit;
                 while (v >= 0 && __ldg(t.ibit + v) >= t.cloud_bit) {
                     const int2 ch = __ldg(t.ichild + v);
                     v = ((cloud >> (__ldg(t.ibit + v) - t.cloud_bit)) & 1) ? ch.y : ch.x;
@@ -311,7 +316,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
             if (ok) {
                 int4 lo, hi;
                 node_box(t, v, lo, hi);
-                search_down<DIM, K, FLOAT>(t, v, M::template boxd<DIM>(q, lo, hi), -1, q, bd, bi, status);
+                search_down<DIM, K, FLOAT>(t, v, M::template boxd<DIM>(q, lo, hi), self, q, bd, bi, status);
             }
         } else {
             int leaf;
@@ -319,7 +324,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
                 leaf = __ldg(t.leaf_of + qi);
             } else {
                 // bit-based: descend by the query's Morton bits (Sec. 2)
-                const u64 key = __ldg(a.qkey + qi);
+                const u64 key = __ldg(qkeys + qi);
                 int v = root;
                 while (v >= 0) {
                     const int2 ch = __ldg(t.ichild + v);
@@ -333,7 +338,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
             int par = __ldg(t.lparent + leaf);
             while (par >= 0 && __ldg(t.ibit + par) < t.cloud_bit) {
                 int4 lo, hi;
-                if (!FLOAT && a.mode == ZD_SEARCH_LEAF) {
+                if (!FLOAT && a.allpts) {
                     // the query lies in the node's Morton cell, which holds
                     // every point the node can hold: stop on the cell
                     if (cell_inside<DIM>(qp, a.shift, __ldg(t.ibit + par), (long long)bd[K - 1])) break;

@@ -1,0 +1,393 @@
+// knn_wide.cuh -- exact k-NN for large k (32 < k <= 128): one warp per query
+// (Algorithms 2 and 3).
+//
+// The k best of a query do not fit one thread's registers, so a whole warp
+// serves one query and spreads its k-best list over the lanes: slot
+// e = 32 r + lane lives in register r of that lane.  The list is kept sorted
+// by (squared distance, id) over e and aligned to the end: the j-th best is
+// slot 32 R - k + j, so the k-th best is always register R - 1 of lane 31,
+// and slots below 32 R - k hold sentinels that order before every point.  The traversal -- scan the start leaf,
+// climb, search siblings down with a box test against the k-th distance --
+// is the one of the one-thread-per-query kernel, executed in lockstep by the
+// warp (every branch depends only on warp-uniform values); the DFS stack is
+// spread over the lanes as well.  Leaves are scanned 32 points at a time,
+// one point per lane.
+//
+// Filling: until k candidates have been seen the k-th distance is infinite
+// and every candidate enters, so the first candidates are appended unsorted
+// to a per-warp shared-memory buffer and sorted once (a bitonic sort over
+// the 32 R register slots) when the k-th arrives.  After that a candidate
+// that beats the k-th best is inserted by the warp: its rank comes from one
+// ballot per register, and the slots from the rank up move up by one place
+// (a shuffle, lane 0 taking lane 31 of the register below), which drops the
+// old k-th best off the top.
+#pragma once
+
+#include "knn_impl.cuh"
+
+namespace zdk {
+
+constexpr int WIDE_WARPS = 4;      // queries in flight per block
+constexpr int WIDE_STACK_REGS = 3; // DFS stack: 96 entries spread over the lanes
+constexpr unsigned WFULL = 0xffffffffu;
+
+template <typename D>
+__device__ __forceinline__ bool wkey_lt(D a, int ai, D b, int bi)
+{
+    return a < b || (a == b && ai < bi);
+}
+
+// Order the pair (a, b): a <= b when up, a >= b otherwise.
+template <typename D>
+__device__ __forceinline__ void wcmpx(D &ad, int &ai, D &bd, int &bi, bool up)
+{
+    const bool sw = up ? wkey_lt(bd, bi, ad, ai) : wkey_lt(ad, ai, bd, bi);
+    if (sw) {
+        const D td = ad;
+        const int ti = ai;
+        ad = bd;
+        ai = bi;
+        bd = td;
+        bi = ti;
+    }
+}
+
+// One stage of a bitonic sort over the 32 R entries: compare-exchange e with
+// e ^ STRIDE, ascending where bit SIZE of e is clear.  Strides of 32 and more
+// pair registers of one lane, smaller strides pair lanes (shuffles).
+template <int SIZE, int STRIDE, int R, typename D>
+__device__ __forceinline__ void wide_stage(D (&d)[R], int (&id)[R], int lane)
+{
+    if constexpr (STRIDE >= 32) {
+        constexpr int s = STRIDE >> 5;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (!(r & s)) wcmpx(d[r], id[r], d[r | s], id[r | s], ((r * 32) & SIZE) == 0);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const D pd = __shfl_xor_sync(WFULL, d[r], STRIDE);
+            const int pi = __shfl_xor_sync(WFULL, id[r], STRIDE);
+            const bool up = ((r * 32 + lane) & SIZE) == 0;
+            const bool keep_min = ((lane & STRIDE) == 0) == up;
+            if (wkey_lt(pd, pi, d[r], id[r]) == keep_min) {
+                d[r] = pd;
+                id[r] = pi;
+            }
+        }
+    }
+    if constexpr (STRIDE > 1) wide_stage<SIZE, STRIDE / 2, R>(d, id, lane);
+}
+
+// Bitonic sort of the 32 R entries (R a power of two), ascending in e.
+template <int SIZE, int R, typename D>
+__device__ __forceinline__ void wide_sort(D (&d)[R], int (&id)[R], int lane)
+{
+    wide_stage<SIZE, SIZE / 2, R>(d, id, lane);
+    if constexpr (SIZE < 32 * R) wide_sort<SIZE * 2, R>(d, id, lane);
+}
+
+template <int DIM, int R, bool FLOAT>
+struct WideQuery {
+    typedef Metric<FLOAT> M;
+    typedef typename M::D D;
+
+    const TreeView &t;
+    typename M::Q q;
+    int self;  // sorted position to skip (all-points), else -1
+    int lane;
+    int k, off; // k, and the slot of the best (32 R - k)
+    D d[R];
+    int id[R];
+    D td; // the k-th best (warp-uniform): infinite while filling
+    int ti;
+    bool filling;
+    int count; // entries appended while filling
+    D *bufd;   // this warp's fill buffer [32 R]
+    int *bufi;
+
+    __device__ WideQuery(const TreeView &t_, int k_, int lane_, D *bd, int *bi)
+        : t(t_), self(-1), lane(lane_), k(k_), off(32 * R - k_), td(M::inf()),
+          ti(INT_MAX), filling(true), count(0), bufd(bd), bufi(bi)
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            d[r] = M::inf();
+            id[r] = INT_MAX;
+        }
+    }
+
+    __device__ __forceinline__ void refresh_kth()
+    {
+        td = __shfl_sync(WFULL, d[R - 1], 31);
+        ti = __shfl_sync(WFULL, id[R - 1], 31);
+    }
+
+    // Move the fill buffer into slots off .. off + count - 1 (sentinels
+    // below, infinite entries above) and sort.
+    __device__ __forceinline__ void finish_fill()
+    {
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = r * 32 + lane - off;
+            d[r] = j < 0 ? D(-1) : j < count ? bufd[j] : M::inf();
+            id[r] = j < 0 ? -1 : j < count ? bufi[j] : INT_MAX;
+        }
+        __syncwarp();
+        wide_sort<2, R>(d, id, lane);
+        filling = false;
+        refresh_kth();
+    }
+
+    // Insert (cd, ci), which beats the k-th best, keeping the list sorted.
+    __device__ __forceinline__ void insert(D cd, int ci)
+    {
+        int pos = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) pos += __popc(__ballot_sync(WFULL, wkey_lt(d[r], id[r], cd, ci)));
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) {
+            if ((r + 1) * 32 <= pos) break; // registers below are unchanged
+            D ud = __shfl_up_sync(WFULL, d[r], 1);
+            int ui = __shfl_up_sync(WFULL, id[r], 1);
+            if (r > 0) {
+                const D cd2 = __shfl_sync(WFULL, d[r - 1], 31);
+                const int ci2 = __shfl_sync(WFULL, id[r - 1], 31);
+                if (lane == 0) {
+                    ud = cd2;
+                    ui = ci2;
+                }
+            }
+            const int e = r * 32 + lane;
+            if (e == pos) {
+                d[r] = cd;
+                id[r] = ci;
+            } else if (e > pos) {
+                d[r] = ud;
+                id[r] = ui;
+            }
+        }
+        refresh_kth();
+    }
+
+    __device__ __forceinline__ void scan_leaf(int leaf)
+    {
+        const int lo = __ldg(t.leaf_lo + leaf), hi = __ldg(t.leaf_lo + leaf + 1);
+        for (int base = lo; base < hi; base += 32) {
+            const int p = base + lane;
+            D cd = M::inf();
+            int ci = INT_MAX;
+            bool ok = false;
+            if (p < hi && p != self) {
+                const int4 c = __ldg(t.pts + p);
+                cd = M::template dist<DIM>(q, c);
+                ci = c.w;
+                ok = wkey_lt(cd, ci, td, ti);
+            }
+            unsigned mask = __ballot_sync(WFULL, ok);
+            if (filling) {
+                const int room = k - count;
+                const int rank = __popc(mask & ((1u << lane) - 1u));
+                if (ok && rank < room) {
+                    bufd[count + rank] = cd;
+                    bufi[count + rank] = ci;
+                }
+                const int n = __popc(mask);
+                const int placed = min(n, room);
+                count += placed;
+                mask = __ballot_sync(WFULL, ok && rank >= placed);
+                if (count >= k || mask) finish_fill();
+            }
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const D xd = __shfl_sync(WFULL, cd, src);
+                const int xi = __shfl_sync(WFULL, ci, src);
+                if (wkey_lt(xd, xi, td, ti)) insert(xd, xi);
+            }
+        }
+    }
+
+    // searchDown (Algorithm 2) from node v whose box distance is dv.
+    __device__ __forceinline__ bool search_down(int v, D dv, u32 *status)
+    {
+        int sn[WIDE_STACK_REGS];
+        D sd[WIDE_STACK_REGS];
+#pragma unroll
+        for (int r = 0; r < WIDE_STACK_REGS; ++r) {
+            sn[r] = 0;
+            sd[r] = D(0);
+        }
+        int sp = 0;
+        auto push = [&](int u, D du) {
+            const int reg = sp >> 5, ln = sp & 31;
+#pragma unroll
+            for (int r = 0; r < WIDE_STACK_REGS; ++r)
+                if (r == reg && lane == ln) {
+                    sn[r] = u;
+                    sd[r] = du;
+                }
+            ++sp;
+        };
+        push(v, dv);
+        while (sp > 0) {
+            --sp;
+            const int reg = sp >> 5, ln = sp & 31;
+            int u0 = sn[0];
+            D d0 = sd[0];
+#pragma unroll
+            for (int r = 1; r < WIDE_STACK_REGS; ++r)
+                if (r == reg) {
+                    u0 = sn[r];
+                    d0 = sd[r];
+                }
+            const int u = __shfl_sync(WFULL, u0, ln);
+            const D du = __shfl_sync(WFULL, d0, ln);
+            if (du > td) continue; // pruned by the (possibly shrunk) k-th distance
+            if (u < 0) {
+                scan_leaf(~u);
+                continue;
+            }
+            const int2 ch = __ldg(t.ichild + u);
+            int4 al, ah, bl, bh;
+            node_box(t, ch.x, al, ah);
+            node_box(t, ch.y, bl, bh);
+            const D da = M::template boxd<DIM>(q, al, ah);
+            const D db = M::template boxd<DIM>(q, bl, bh);
+            const int nf = da <= db ? ch.y : ch.x, nn = da <= db ? ch.x : ch.y;
+            const D df = da <= db ? db : da, dn = da <= db ? da : db;
+            if (sp + 2 > 32 * WIDE_STACK_REGS) {
+                if (lane == 0) set_status(status, ZD_ERR_CUDA);
+                return false;
+            }
+            if (df <= td) push(nf, df);
+            if (dn <= td) push(nn, dn);
+        }
+        return true;
+    }
+};
+
+template <int DIM, int R, bool FLOAT>
+__global__ void __launch_bounds__(32 * WIDE_WARPS, 4) k_knn_wide(KnnArgs a, u32 *status)
+{
+    typedef Metric<FLOAT> M;
+    typedef typename M::D D;
+    __shared__ D s_bufd[WIDE_WARPS][32 * R];
+    __shared__ int s_bufi[WIDE_WARPS][32 * R];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const TreeView &t = a.t;
+    const int nl = __ldg(t.meta);
+    const int root = nl > 1 ? 0 : ~0;
+
+    for (int64_t qi = (int64_t)blockIdx.x * WIDE_WARPS + warp; qi < a.m;
+         qi += (int64_t)gridDim.x * WIDE_WARPS) {
+        __syncwarp();
+        WideQuery<DIM, R, FLOAT> w(t, a.k, lane, s_bufd[warp], s_bufi[warp]);
+        int4 qp;
+        int64_t row;
+        if (a.allpts) {
+            qp = __ldg(t.pts + qi);
+            w.self = (int)qi;
+            row = qp.w;
+            if (t.cloud_off) row += __ldg(t.cloud_off + (__ldg(t.keys + qi) >> t.cloud_bit));
+        } else {
+            qp = __ldg(a.q + qi);
+            row = qp.w;
+        }
+        w.q = M::make(qp);
+
+        bool ok = true;
+        if (t.n > 0) {
+            if (a.mode == ZD_SEARCH_ROOT) {
+                int v = root;
+                bool has = true;
+                if (t.cloud_off) {
+                    // descend to the root of the query's own cloud
+                    const u64 cloud = __ldg((a.allpts ? t.keys : a.qkey) + qi) >> t.cloud_bit;
+                    while (v >= 0 && __ldg(t.ibit + v) >= t.cloud_bit) {
+                        const int2 ch = __ldg(t.ichild + v);
+                        v = ((cloud >> (__ldg(t.ibit + v) - t.cloud_bit)) & 1) ? ch.y : ch.x;
+                    }
+                    const int first = v >= 0 ? __ldg(t.irange + v).x : __ldg(t.leaf_lo + ~v);
+                    const int last = v >= 0 ? __ldg(t.irange + v).y : __ldg(t.leaf_lo + ~v + 1);
+                    has = last > first && (__ldg(t.keys + first) >> t.cloud_bit) == cloud;
+                }
+                if (has) {
+                    int4 lo, hi;
+                    node_box(t, v, lo, hi);
+                    ok = w.search_down(v, M::template boxd<DIM>(w.q, lo, hi), status);
+                }
+            } else {
+                int leaf;
+                if (a.mode == ZD_SEARCH_LEAF) {
+                    leaf = __ldg(t.leaf_of + qi);
+                } else {
+                    // bit-based: descend by the query's Morton bits (Sec. 2)
+                    const u64 key = __ldg((a.allpts ? t.keys : a.qkey) + qi);
+                    int v = root;
+                    while (v >= 0) {
+                        const int2 ch = __ldg(t.ichild + v);
+                        v = ((key >> __ldg(t.ibit + v)) & 1) ? ch.y : ch.x;
+                    }
+                    leaf = ~v;
+                }
+                // searchUp (Algorithm 3)
+                w.scan_leaf(leaf);
+                int node = ~leaf;
+                int par = __ldg(t.lparent + leaf);
+                while (ok && par >= 0 && __ldg(t.ibit + par) < t.cloud_bit) {
+                    int4 lo, hi;
+                    if (!FLOAT && a.allpts) {
+                        if (cell_inside<DIM>(qp, a.shift, __ldg(t.ibit + par), (long long)w.td)) break;
+                    } else {
+                        node_box(t, node, lo, hi);
+                        if (M::template inside<DIM>(w.q, lo, hi, w.td)) break;
+                    }
+                    const int2 ch = __ldg(t.ichild + par);
+                    const int sib = ch.x == node ? ch.y : ch.x;
+                    node_box(t, sib, lo, hi);
+                    const D ds = M::template boxd<DIM>(w.q, lo, hi);
+                    if (ds <= w.td) ok = w.search_down(sib, ds, status);
+                    node = par;
+                    par = __ldg(t.iparent + par);
+                }
+            }
+        }
+        if (w.filling) w.finish_fill();
+
+        const int k = a.k;
+        int32_t *oi = a.out_idx + row * k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = r * 32 + lane - w.off;
+            if (e >= 0) oi[e] = w.d[r] < M::inf() ? w.id[r] : -1;
+        }
+        if (a.out_dist) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int e = r * 32 + lane - w.off;
+                if (e < 0) continue;
+                if (FLOAT)
+                    ((float *)a.out_dist)[row * k + e] =
+                        w.d[r] < M::inf() ? (float)sqrt((double)w.d[r]) : __int_as_float(0x7f800000);
+                else
+                    ((long long *)a.out_dist)[row * k + e] = (long long)w.d[r];
+            }
+        }
+    }
+}
+
+template <int DIM, bool FLOAT>
+int launch_knn_wide_dim(const KnnArgs &a, cudaStream_t s)
+{
+    if (a.m <= 0) return ZD_OK;
+    u32 *st = status_word();
+    const unsigned grid = grid_for(a.m, WIDE_WARPS, 152 * 64);
+    if (a.k <= 64) k_knn_wide<DIM, 2, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
+    else k_knn_wide<DIM, 4, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+} // namespace zdk

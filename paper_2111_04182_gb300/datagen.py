@@ -17,6 +17,13 @@ these recipes stand in for them with the same shapes:
 * ``warped_pair``  -- a pair of float32 clouds, N(0, 1) coordinates pushed
   through one random affine map x -> R diag(s) x + t (R a random rotation,
   s log-uniform in [0.5, 2], t ~ N(0, 1)).
+* ``plummer``      -- 3D Plummer sphere (the paper's skewed 3D set, Sec. 5
+  "Test data"): radius from the inverted cumulative mass profile, isotropic
+  direction, truncated and scaled onto the integer grid.
+* ``kuzmin``       -- 2D Kuzmin disc (the paper's skewed 2D set): radius from
+  the inverted cumulative surface mass, uniform angle, truncated and scaled.
+* ``on_sphere``    -- points on the surface of a sphere (the paper's 3D
+  "on sphere" set), rounded to the grid.
 """
 from __future__ import annotations
 
@@ -77,6 +84,67 @@ def warped_pair(rng: np.random.Generator, na: int, nb: int, dim: int = 3):
     return a.astype(np.float32), b.astype(np.float32)
 
 
+def _isotropic(rng: np.random.Generator, n: int, dim: int) -> np.ndarray:
+    """Unit vectors uniform on the sphere (normalised Gaussian vectors)."""
+    v = rng.standard_normal((n, dim))
+    nrm = np.linalg.norm(v, axis=1)
+    bad = nrm == 0
+    while bad.any():
+        v[bad] = rng.standard_normal((int(bad.sum()), dim))
+        nrm[bad] = np.linalg.norm(v[bad], axis=1)
+        bad = nrm == 0
+    return v / nrm[:, None]
+
+
+def _truncated_radii(rng: np.random.Generator, n: int, inv_cdf, r_max: float) -> np.ndarray:
+    """Radii drawn by inverting a cumulative mass profile, redrawn above r_max."""
+    r = inv_cdf(rng.uniform(0.0, 1.0, n))
+    bad = ~(r <= r_max)
+    while bad.any():
+        r[bad] = inv_cdf(rng.uniform(0.0, 1.0, int(bad.sum())))
+        bad = ~(r <= r_max)
+    return r
+
+
+def _to_grid(x: np.ndarray, bits: int) -> np.ndarray:
+    top = (1 << bits) - 1
+    return np.clip(np.rint(x), 0, top).astype(np.int32)
+
+
+def plummer(rng: np.random.Generator, n: int, bits: int = 20, r_max: float = 256.0) -> np.ndarray:
+    """Plummer sphere of scale radius 1: the mass inside radius r is
+    r^3 / (1 + r^2)^(3/2), so r = (u^(-2/3) - 1)^(-1/2) for u ~ U(0, 1)
+    (Aarseth, Henon and Wielen 1974).  Radii above r_max scale radii are
+    redrawn; the ball of radius r_max fills the grid [0, 2^bits)^3."""
+    def inv(u):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            return 1.0 / np.sqrt(u ** (-2.0 / 3.0) - 1.0)
+    half = (1 << (bits - 1)) - 1
+    r = _truncated_radii(rng, n, inv, r_max)
+    x = (1 << (bits - 1)) + _isotropic(rng, n, 3) * (r * (half / r_max))[:, None]
+    return _to_grid(x, bits)
+
+
+def kuzmin(rng: np.random.Generator, n: int, bits: int = 30, r_max: float = 4096.0) -> np.ndarray:
+    """Kuzmin disc of scale length 1: the mass inside radius R is
+    1 - 1 / sqrt(1 + R^2), so R = sqrt((1 - u)^(-2) - 1) for u ~ U(0, 1).
+    Radii above r_max scale lengths are redrawn; the disc of radius r_max
+    fills the grid [0, 2^bits)^2."""
+    def inv(u):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            return np.sqrt((1.0 - u) ** -2.0 - 1.0)
+    half = (1 << (bits - 1)) - 1
+    r = _truncated_radii(rng, n, inv, r_max)
+    x = (1 << (bits - 1)) + _isotropic(rng, n, 2) * (r * (half / r_max))[:, None]
+    return _to_grid(x, bits)
+
+
+def on_sphere(rng: np.random.Generator, n: int, bits: int = 20) -> np.ndarray:
+    """Points uniform on the sphere inscribed in [0, 2^bits)^3."""
+    half = (1 << (bits - 1)) - 1
+    return _to_grid((1 << (bits - 1)) + _isotropic(rng, n, 3) * half, bits)
+
+
 # --------------------------------------------------------------------------
 # The five workloads.  Each returns plain numpy arrays plus its parameters.
 # --------------------------------------------------------------------------
@@ -91,6 +159,31 @@ def workload_3d_clustered(n: int = 10_000_000, seed: int = 1, n_clusters: int = 
     """3D, int32 in [0, 2^20)^3 from 1000 Gaussian clusters, L = 16, k = 10."""
     rng = np.random.default_rng(seed)
     return dict(pts=clustered(rng, n, 3, n_clusters, 20), dim=3, coord_bits=21, leaf_size=16, k=10)
+
+
+def workload_3d_uniform(n: int = 10_000_000, k: int = 100, seed: int = 5):
+    """3D, int32 uniform in [0, 2^20)^3, L = 16: the uniform cube of the
+    paper's k sweep (Sec. 5, k up to 100), at a large k."""
+    rng = np.random.default_rng(seed)
+    return dict(pts=uniform(rng, n, 3, 20), dim=3, coord_bits=21, leaf_size=16, k=k)
+
+
+# The five point sets of the paper's search-start comparison (Sec. 5, k = 1):
+# name -> (generator, dim, coord_bits of the tree, seed).
+SKEWED_SETS = {
+    "2DinCube": (lambda rng, n: uniform(rng, n, 2, 20), 2, 20, 6),
+    "2Dkuzmin": (lambda rng, n: kuzmin(rng, n, 30), 2, 30, 7),
+    "3DonSphere": (lambda rng, n: on_sphere(rng, n, 20), 3, 21, 8),
+    "3DinCube": (lambda rng, n: uniform(rng, n, 3, 20), 3, 21, 9),
+    "3Dplummer": (lambda rng, n: plummer(rng, n, 20), 3, 21, 10),
+}
+
+
+def workload_skewed(name: str, n: int = 10_000_000, k: int = 1):
+    """One of the five point sets of the search-start comparison; L = 16."""
+    gen, dim, bits, seed = SKEWED_SETS[name]
+    rng = np.random.default_rng(seed)
+    return dict(pts=gen(rng, n), dim=dim, coord_bits=bits, leaf_size=16, k=k, name=name)
 
 
 class DynamicWorkload:

@@ -23,7 +23,8 @@ ZD_ERR_UNIMPLEMENTED, ZD_ERR_CAPACITY = 8, 9
 ZD_COORD_I32, ZD_COORD_F32 = 0, 1
 ZD_SEARCH_LEAF, ZD_SEARCH_BIT, ZD_SEARCH_ROOT = 0, 1, 2
 ZD_KNN_THREAD_PER_QUERY, ZD_KNN_WARP_GROUP = 0x100, 0x200
-ZD_MAX_K = 32
+ZD_KNN_ALL_POINTS = 0x400
+ZD_MAX_K = 128
 
 EXPORTED = ["zd_status_string", "zd_check", "zd_selftest_wait_timeout", "zd_morton_encode", "zd_morton_sort", "zd_morton_sort_noalloc",
             "zd_build",
@@ -233,7 +234,8 @@ class ZdTree:
             raise RuntimeError("use zd_knn_batched for a forest")
         ddt = torch.float32 if self.is_float else torch.int64
         if queries is None:
-            mode = ZD_SEARCH_LEAF
+            # all points; a bit- or root-based start is asked for explicitly
+            mode = ZD_SEARCH_LEAF if mode in (None, ZD_SEARCH_LEAF) else mode | ZD_KNN_ALL_POINTS
             rows = self.info(stream)["next_id"] if out is None else None
             qp, m = None, 0
         else:

@@ -67,3 +67,28 @@ def test_no_host_fallback_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(zd, "_LIB", None)
     with pytest.raises(RuntimeError):
         zd._lib()
+
+
+def test_binding_constants_match_header():
+    """Every integer constant of the header (enum members and #defines) has
+    the same value in the Python binding."""
+    from paper_2111_04182_gb300 import zd
+    src = open(os.path.join(ROOT, "include", "zd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\w*\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"\b(ZD_\w+)\s*=\s*([^,\s]+)", body):
+            consts[name] = int(val, 0)
+    for name, val, sh in re.findall(r"#define\s+(ZD_\w+)[ \t]+\(?([0-9x]+)(?:\s*<<\s*(\d+))?", src):
+        consts[name] = int(val, 0) << int(sh or 0)
+    assert len(consts) > 15
+    for name, val in consts.items():
+        assert getattr(zd, name) == val, name
+
+
+def test_bench_runs_the_oracle_only_for_the_cpu_baseline():
+    """bench.py imports the oracle in its CPU-baseline function only."""
+    text = open(os.path.join(ROOT, "bench.py")).read()
+    funcs = re.split(r"\ndef ", text)
+    users = [f.split("(")[0] for f in funcs if "from oracle import" in f or "import oracle" in f]
+    assert users == ["cpu_baseline"], users

@@ -47,7 +47,7 @@ def test_host_checked_errors(zd):
     assert e.value.code == zd.ZD_ERR_INVALID_ARG
     t = zd.zd_build(pts, 16, 21)
     with pytest.raises(zd.ZdError) as e:
-        t.knn(33)
+        t.knn(zd.ZD_MAX_K + 1)
     assert e.value.code == zd.ZD_ERR_UNIMPLEMENTED
     with pytest.raises(zd.ZdError):
         zd.zd_selftest_wait_timeout(0)

@@ -146,6 +146,62 @@ def test_knn_all_points(zd, oracle, dim, k, mapping):
     t.free()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("k", [1, 10, 40])
+def test_knn_graph_three_starts(zd, oracle, dim, k):
+    """The k-NN graph computed leaf-based, bit-based and root-based (the
+    paper's three algorithms) is the same exact answer."""
+    rng = np.random.default_rng(dim * 10 + k)
+    bits = 21 if dim == 3 else 20
+    c = rng.integers(0, 2 ** 19, size=(6, dim))
+    pts = np.clip(c[rng.integers(0, 6, 20_000)] + rng.normal(0, 1500, (20_000, dim)), 0, 2 ** 19).astype(np.int32)
+    pts[:200] = pts[200:400]
+    t = zd.zd_build(_t(pts), 16, bits)
+    oi, od = oracle.OracleTree(pts, 16, bits).knn(k)
+    for mode in (zd.ZD_SEARCH_LEAF, zd.ZD_SEARCH_BIT, zd.ZD_SEARCH_ROOT):
+        idx, d2 = t.knn(k, mode=mode)
+        assert zd.zd_check() == 0
+        assert np.array_equal(idx.cpu().numpy(), oi), mode
+        assert np.array_equal(d2.cpu().numpy(), od), mode
+    t.free()
+
+
+@pytest.mark.parametrize("name", ["2DinCube", "2Dkuzmin", "3DonSphere", "3DinCube", "3Dplummer"])
+def test_skewed_sets_tree_and_all_starts(zd, oracle, name):
+    """The five point sets of the paper's search-start comparison (skewed
+    Plummer and Kuzmin sets, a sphere surface, uniform square and cube): the
+    canonical tree and the k-NN graph from every start and mapping equal the
+    oracle's."""
+    from paper_2111_04182_gb300 import datagen
+    w = datagen.workload_skewed(name, n=30_000)
+    pts, bits = w["pts"], w["coord_bits"]
+    t = zd.zd_build(_t(pts), 16, bits)
+    ot = oracle.OracleTree(pts, 16, bits)
+    o, g = ot.canonical_dump(), canonical(nodes_of(t.export()))
+    assert np.array_equal(g["lo"], o["lo"]) and np.array_equal(g["bit"], o["bit"])
+    for k in (1, 8):
+        oi, od = ot.knn(k)
+        for mode, mapping in ((0, 0x100), (0, 0x200), (1, 0), (2, 0)):
+            idx, d2 = t.knn(k, mode=mode, mapping=mapping)
+            assert zd.zd_check() == 0
+            assert np.array_equal(idx.cpu().numpy(), oi), (k, mode, mapping)
+            assert np.array_equal(d2.cpu().numpy(), od), (k, mode, mapping)
+    t.free()
+
+
+def test_float_knn_graph_three_starts(zd, oracle):
+    from paper_2111_04182_gb300 import datagen
+    _, b = datagen.warped_pair(np.random.default_rng(79), 10, 7000)
+    t = zd.zd_build(_t(b), 16, 21)
+    bi, bd = oracle.knn_brute(b, 7)
+    for mode in (zd.ZD_SEARCH_LEAF, zd.ZD_SEARCH_BIT, zd.ZD_SEARCH_ROOT):
+        idx, dist = t.knn(7, mode=mode)
+        assert np.array_equal(idx.cpu().numpy(), bi), mode
+        assert np.allclose(dist.cpu().numpy(), np.sqrt(bd), rtol=1e-6, atol=0)
+    t.free()
+    assert zd.zd_check() == 0
+
+
 @pytest.mark.parametrize("mapping", MAPPINGS)
 def test_knn_saturated_keys_fall_back_exactly(zd, oracle, mapping):
     """Far-apart 2D points with 31-bit coordinates: squared distances exceed
