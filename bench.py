@@ -11,7 +11,8 @@ the timed region starts; L2 is flushed (256 MiB write) between steps.
 
 --impl reference times the CPU oracle (plain C, OpenMP over queries) on the
 host cores on a bounded sample of the same workload.  Other workloads:
---workload 2d-uniform | dynamic | batched | differentiable | large-k | skewed.
+--workload 2d-uniform | dynamic | batched | differentiable | large-k | skewed |
+update-sweep.
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -363,7 +364,7 @@ def _events(n):
 def run_other(args, ws, rank, local):
     fn = {"2d-uniform": bench_2d, "dynamic": bench_dynamic, "batched": bench_batched,
           "differentiable": bench_differentiable, "large-k": bench_large_k,
-          "skewed": bench_skewed}.get(args.workload)
+          "skewed": bench_skewed, "update-sweep": bench_update_sweep}.get(args.workload)
     if fn is None:
         raise SystemExit("unknown workload %r" % args.workload)
     out = fn(args)
@@ -599,6 +600,60 @@ def bench_skewed(args):
             "sets": sets, "all_starts_same_ids": True}
 
 
+def bench_update_sweep(args):
+    """Per-point cost of batch updates and of dynamic queries against the
+    batch size (the paper's update and dynamic-query plots): a 2D tree of
+    10^7 uniform points in [0, 2^20)^2, L = 16; for each batch size b an
+    insert of b uniform points then a delete of those b ids (the set is
+    restored each time), and bit-based k = 1 queries in batches of m.
+    Insert and delete validate on the host (they sync), so their times are
+    whole-call latencies.  At the end the tree must equal a fresh build of
+    the original points (same sorted keys and node structure)."""
+    import torch
+    from paper_2111_04182_gb300 import datagen, zd
+    n0 = args.n
+    rng = np.random.default_rng(11)
+    pts = datagen.uniform(rng, n0, 2, 20)
+    sizes = [b for b in (1, 10, 100, 1_000, 10_000, 100_000, 1_000_000, 5_000_000) if b <= n0]
+    t = zd.zd_build(torch.from_numpy(pts).cuda(), 16, 20, capacity=n0 + max(sizes))
+    ups = []
+    for b in sizes:
+        ins_ms, del_ms = [], []
+        for rep in range(args.warmup + max(1, args.steps // 3)):
+            batch = torch.from_numpy(datagen.uniform(rng, b, 2, 20)).cuda()
+            torch.cuda.synchronize()
+            e = _events(4)
+            e[0].record(); ids = t.insert(batch); e[1].record()
+            e[2].record(); t.delete(ids); e[3].record(); e[3].synchronize()
+            if rep >= args.warmup:
+                ins_ms.append(e[0].elapsed_time(e[1])); del_ms.append(e[2].elapsed_time(e[3]))
+        im, dm = float(np.median(ins_ms)), float(np.median(del_ms))
+        ups.append({"batch": b, "insert_ms": im, "delete_ms": dm, "insert_s_per_point": im / 1e3 / b,
+                    "delete_s_per_point": dm / 1e3 / b})
+    qs = []
+    for m in (1, 100, 10_000, 1_000_000, 10_000_000):
+        q = torch.from_numpy(datagen.uniform(rng, m, 2, 20)).cuda()
+        ms = []
+        for rep in range(args.warmup + max(1, args.steps // 3)):
+            a, b2 = _events(2)
+            a.record(); t.knn(1, queries=q, mode=zd.ZD_SEARCH_BIT); b2.record(); b2.synchronize()
+            if rep >= args.warmup:
+                ms.append(a.elapsed_time(b2))
+        qm = float(np.median(ms))
+        qs.append({"queries": m, "ms": qm, "s_per_query": qm / 1e3 / m})
+    assert zd.zd_check() == 0
+    fresh = zd.zd_build(torch.from_numpy(pts).cuda(), 16, 20)
+    ea, eb = t.export(), fresh.export()
+    same = all(torch.equal(ea[f], eb[f]) for f in ("keys", "leaf_lo", "node_lo", "node_hi", "node_bit"))
+    if not same:
+        raise RuntimeError("updated tree differs from a fresh build of the same points")
+    t.free(); fresh.free()
+    big = ups[-1]
+    return {"workload": "update-sweep-2d-%d" % n0, "metric": "updates/s and dynamic queries/s vs batch size",
+            "value": big["batch"] / (big["insert_ms"] / 1e3), "unit": "updates/s (insert, largest batch)",
+            "updates": ups, "queries": qs, "tree_equals_fresh_build": same}
+
+
 def bench_large_k(args):
     """3D uniform, n = 10^7 in [0, 2^20)^3, L = 16, k = 100 (the paper's k
     sweep): build + all-points k-NN with ids and int64 d^2 written; for
@@ -634,7 +689,8 @@ def bench_large_k(args):
     return {"workload": "3d-uniform-1e7-k%d" % k, "metric": "queries/s (build + all-points k=%d)" % k,
             "value": n / ((bm + km) / 1e3), "unit": "queries/s", "build_ms": bm, "knn_ms": km,
             "knn_queries_per_s": n / (km / 1e3), "k": k, "steps": args.steps,
-            "roofline": {"kernel": "k_knn_wide<3,4,0>", "bound": "hbm", "achieved": kb / (km / 1e3) / 1e9,
+            "roofline": {"kernel": "k_knn_wide<3,%d,0>" % (2 if k <= 64 else 4), "bound": "hbm",
+                         "achieved": kb / (km / 1e3) / 1e9,
                          "peak": pk, "peak_source": pk_src, "unit": "GB/s",
                          "frac": kb / (km / 1e3) / 1e9 / pk, "algorithmic_bytes_per_launch": kb}}
 

@@ -70,7 +70,8 @@ enum { ZD_SEARCH_LEAF = 0, ZD_SEARCH_BIT = 1, ZD_SEARCH_ROOT = 2 };
  * that are consecutive in Morton order, each lane keeping its own k best.
  * Both return the same exact neighbours.  Default (neither flag): warp groups
  * for all points and for external queries at least a quarter as many as the
- * tree's points, one thread per query for sparser queries. */
+ * tree's points when k >= 3 (k >= 16 for integer trees with B > 24), one
+ * thread per query otherwise. */
 enum { ZD_KNN_THREAD_PER_QUERY = 0x100, ZD_KNN_WARP_GROUP = 0x200 };
 
 /* OR-ed into ZD_SEARCH_BIT or ZD_SEARCH_ROOT with d_queries NULL: the k-NN

@@ -580,10 +580,16 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
     if (k > KNN_MAX_K_REG) return launch_knn_wide(a, s);
     // Warp groups serve leaf-based all points and bit-based external queries;
     // all points started from the root or by key bits run one thread per
-    // query (Algorithms 2 / 3 as the paper states them).
+    // query (Algorithms 2 / 3 as the paper states them).  By default groups
+    // run only where they were measured faster: dense query sets (above),
+    // and k >= 3 -- at k <= 2 a query's own traversal is short and the
+    // shared one costs more (10^7 points, k = 1: 4.8 vs 5.3 ms clustered,
+    // 1.7 vs 2.5 ms on the skewed 2D set) -- or k >= 16 for integer trees
+    // without exact float copies (B > 24), whose groups lack the fp32 filter.
     const bool allpts = a.allpts;
     const bool dense = allpts || 4 * m >= t->n;
-    const bool group = (variant == ZD_KNN_WARP_GROUP || (variant == 0 && dense)) &&
+    const bool k_ok = k >= 3 && (t->fpts || t->is_float || k >= 16);
+    const bool group = (variant == ZD_KNN_WARP_GROUP || (variant == 0 && dense && k_ok)) &&
                        (allpts ? mode == ZD_SEARCH_LEAF
                                : ((mode == ZD_SEARCH_BIT && !t->cloud_off) || forest_ext));
     if (!group) return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s);

@@ -18,9 +18,13 @@
 // Each lane keeps its k best as 64-bit keys (d^2 << idb) | id, so the order of
 // keys is the order (d^2, id) and an insertion step is one 64-bit compare.
 // Candidates are first filtered on the plain d^2 against the lane's k-th d^2;
-// only survivors are packed.  d^2 saturates at 2^(64-idb) - 1; a saturated
-// threshold counts as infinite, and a query whose k nearest include a
-// saturated entry is handed to the exact one-thread-per-query kernel.
+// only survivors are packed.  d^2 saturates at sat = 2^(64-idb) - 1, and a
+// lane never searches beyond d^2 = sat - 1: its threshold starts there and
+// stays there while its k-th entry is missing or saturated, so a lane whose
+// neighbours lie that far (sparse outskirts of skewed data) does not drag
+// the whole group through the tree.  A query that ends with a missing or
+// saturated entry among its first k is handed to the exact
+// one-thread-per-query kernel.
 //
 // The climb stops on the node's Morton cell -- the box of all coordinates
 // whose keys share the node's prefix, which contains every point the node can
@@ -74,12 +78,13 @@ struct GroupCtx {
     unsigned sx, sy, sz; // shift
 };
 
-// k-th d^2 of a lane: LLONG_MAX while unknown or saturated.
+// Search radius^2 of a lane: its k-th d^2, or sat - 1 while that entry is
+// missing or saturated.
 template <int K>
 __device__ __forceinline__ long long thr_of(const u64 (&key)[K], const GroupCtx &c)
 {
     const u64 d = key[K - 1] >> c.idb;
-    return d >= c.sat ? LLONG_MAX : (long long)d;
+    return d >= c.sat ? (long long)(c.sat - 1) : (long long)d;
 }
 
 // Float filter threshold: every candidate with d^2 <= thr computes (three
@@ -310,21 +315,16 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
         if (pbit >= t.cloud_bit) break; // never leave the cloud
         bool inside = true;
         if (c.live) {
-            if (thr == LLONG_MAX) {
-                inside = false;
+            // the node's cell: key bits >= pbit are the node's prefix
+            const bool in_cell = allpts || ((c.qkey ^ __ldg(t.keys + node_lo_pos(t, node))) >> pbit) == 0;
+            if (in_cell) {
+                inside = cell_inside<DIM>(make_int4(c.qx, c.qy, c.qz, 0), make_uint3(c.sx, c.sy, c.sz), pbit,
+                                          thr);
             } else {
-                // the node's cell: key bits >= pbit are the node's prefix
-                const bool in_cell =
-                    allpts || ((c.qkey ^ __ldg(t.keys + node_lo_pos(t, node))) >> pbit) == 0;
-                if (in_cell) {
-                    inside = cell_inside<DIM>(make_int4(c.qx, c.qy, c.qz, 0), make_uint3(c.sx, c.sy, c.sz),
-                                              pbit, thr);
-                } else {
-                    int4 lo, hi;
-                    node_box(t, node, lo, hi);
-                    inside = axis_inside(c.qx, lo.x, hi.x, thr) && axis_inside(c.qy, lo.y, hi.y, thr) &&
-                             (DIM == 2 || axis_inside(c.qz, lo.z, hi.z, thr));
-                }
+                int4 lo, hi;
+                node_box(t, node, lo, hi);
+                inside = axis_inside(c.qx, lo.x, hi.x, thr) && axis_inside(c.qy, lo.y, hi.y, thr) &&
+                         (DIM == 2 || axis_inside(c.qz, lo.z, hi.z, thr));
             }
         }
         if (__all_sync(0xffffffffu, inside)) break;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
     u64 key[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) key[j] = ~0ull;
-    long long thr = LLONG_MAX;
+    long long thr = (long long)(c.sat - 1);
     float thr_f = thr_float(thr);
 
     if (t.n > 0) group_traverse<DIM, K, FS>(t, a, c, key, thr, thr_f, g0, gend, allpts, stack, status);
@@ -384,11 +384,12 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
 
     if (!c.live) return;
     const int k = a.k;
-    // a saturated entry among the first k: exact fallback
+    // an entry among the first k that is missing (empty slots read as
+    // saturated) or saturated: exact fallback
     bool saturated = false; // static indices keep the list in registers
 #pragma unroll
     for (int j = 0; j < K; ++j)
-        saturated = saturated || (j < k && key[j] != ~0ull && (key[j] >> c.idb) >= c.sat);
+        saturated = saturated || (j < k && (key[j] >> c.idb) >= c.sat);
     if (saturated) {
         const int slot = atomicAdd(a.fix_count, 1);
         a.fix_list[slot] = qi;

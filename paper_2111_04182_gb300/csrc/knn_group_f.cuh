@@ -4,7 +4,9 @@
 //
 // Neighbours are ranked exactly as the oracle ranks them: by (D, id) with
 // D = ((dx*dx + dy*dy) + dz*dz) in fp64, dx = (double)q.x - (double)p.x, no
-// contraction.  Each lane keeps its k best as (D, id) pairs.  Candidates are
+// contraction.  Each lane keeps its k best as (D, id) pairs, D held as the
+// int64 bit pattern of the double (ordered like the value) so that list
+// comparisons avoid the fp64 pipe.  Candidates are
 // first filtered in fp32: the fp32 estimate of D carries a relative error
 // below 2^-20 (two roundings of each difference and square, three of the
 // sum), so a candidate with D <= thr always has estimate <= thr * (1 + 2^-18)
@@ -24,12 +26,6 @@ struct GroupCtxF {
     bool live;
 };
 
-__device__ __forceinline__ float thr_float_f(double thr)
-{
-    if (!(thr < __longlong_as_double(0x7ff0000000000000ll))) return __int_as_float(0x7f800000);
-    return __fmul_ru(__double2float_ru(thr), 1.0f + 1.0f / 262144.0f);
-}
-
 template <int DIM>
 __device__ __forceinline__ double exact_d2(const GroupCtxF &c, float4 p)
 {
@@ -43,11 +39,11 @@ __device__ __forceinline__ double exact_d2(const GroupCtxF &c, float4 p)
 }
 
 template <int DIM, int K>
-__device__ __forceinline__ void accept_f(int p, float4 pt, const GroupCtxF &c, double (&bd)[K], int (&bi)[K],
+__device__ __forceinline__ void accept_f(int p, float4 pt, const GroupCtxF &c, long long (&bd)[K], int (&bi)[K],
                                          float &thr_f)
 {
     if (p == c.self) return;
-    const double d = exact_d2<DIM>(c, pt);
+    const long long d = __double_as_longlong(exact_d2<DIM>(c, pt));
     const int id = __float_as_int(pt.w);
     if (d < bd[K - 1] || (d == bd[K - 1] && id < bi[K - 1])) {
         kb_insert<K>(bd, bi, d, id);
@@ -64,7 +60,7 @@ __device__ __forceinline__ float est_d2(const GroupCtxF &c, float4 p)
 
 template <int DIM, int K>
 __device__ __forceinline__ void group_scan_ff(const TreeView &t, int a, int b, const GroupCtxF &c,
-                                              double (&bd)[K], int (&bi)[K], float &thr_f)
+                                              long long (&bd)[K], int (&bi)[K], float &thr_f)
 {
     const float4 *pts = (const float4 *)t.pts;
     int p = a;
@@ -99,7 +95,7 @@ __device__ __forceinline__ float box_est(const GroupCtxF &c, float4 lo, float4 h
 
 template <int DIM, int K>
 __device__ __forceinline__ void group_search_ff(const TreeView &t, int start, int l0, int l1, u64 mid_key,
-                                                int *stack, const GroupCtxF &c, double (&bd)[K], int (&bi)[K],
+                                                int *stack, const GroupCtxF &c, long long (&bd)[K], int (&bi)[K],
                                                 float &thr_f, u32 *status)
 {
     const int lane = threadIdx.x & 31;
@@ -164,7 +160,7 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group_f(KnnArgs a, u32 *sta
     c.dz = (double)c.fz;
     c.self = allpts && c.live ? qi : -1;
     const u64 qkey = allpts ? __ldg(t.keys + qs) : __ldg(a.qkey + qs);
-    double bd[K];
+    long long bd[K];
     int bi[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -230,7 +226,7 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group_f(KnnArgs a, u32 *sta
         if (j < k) {
             const bool have = bd[j] < M::inf();
             oi[j] = have ? bi[j] : -1;
-            if (od) od[j] = have ? (float)sqrt(bd[j]) : __int_as_float(0x7f800000);
+            if (od) od[j] = have ? M::out_dist(bd[j]) : __int_as_float(0x7f800000);
         }
     }
 }

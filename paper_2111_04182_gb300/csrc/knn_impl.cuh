@@ -44,6 +44,7 @@ struct Metric<false> {
         int x, y, z;
     };
     __device__ static D inf() { return LLONG_MAX; }
+    __device__ static float out_dist(D) { return 0.f; } // integer trees report d^2
     __device__ static Q make(int4 p) { return Q{p.x, p.y, p.z}; }
     template <int DIM>
     __device__ static D dist(const Q &q, int4 p)
@@ -90,14 +91,19 @@ struct Metric<false> {
 
 // Float coordinates: the ranking value is an fp64 squared distance evaluated
 // as ((dx*dx + dy*dy) + dz*dz), dx = (double)q.x - (double)p.x, each
-// operation rounded to nearest with no contraction.
+// operation rounded to nearest with no contraction.  The value travels as
+// the bit pattern of the (non-negative) double read as an int64: for
+// non-negative doubles and +inf the patterns are ordered like the values, so
+// every comparison runs on the integer pipe, not the much narrower fp64 one.
 template <>
 struct Metric<true> {
-    typedef double D;
+    typedef long long D;
     struct Q {
         double x, y, z;
     };
-    __device__ static D inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    __device__ static D inf() { return 0x7ff0000000000000ll; }
+    __device__ static D bits(double v) { return __double_as_longlong(v); }
+    __device__ static float out_dist(D d) { return (float)sqrt(__longlong_as_double(d)); }
     __device__ static Q make(int4 p)
     {
         return Q{(double)__int_as_float(p.x), (double)__int_as_float(p.y), (double)__int_as_float(p.z)};
@@ -112,14 +118,15 @@ struct Metric<true> {
             double dz = __dsub_rn(q.z, (double)__int_as_float(p.z));
             s = __dadd_rn(s, __dmul_rn(dz, dz));
         }
-        return s;
+        return bits(s);
     }
+    // Distance from q to [lo, hi] along one axis: l - q if q < l, q - h if
+    // q > h, else 0 (a rounded difference of distinct doubles is never 0, so
+    // its sign decides the case).
     __device__ static double gap(double q, float lo, float hi)
     {
-        double l = (double)lo, h = (double)hi;
-        if (q < l) return __dsub_rn(l, q);
-        if (q > h) return __dsub_rn(q, h);
-        return 0.0;
+        const double a = __dsub_rn((double)lo, q), b = __dsub_rn(q, (double)hi);
+        return bits(a) > 0 ? a : (bits(b) > 0 ? b : 0.0);
     }
     template <int DIM>
     __device__ static D boxd(const Q &q, int4 lo, int4 hi)
@@ -131,16 +138,18 @@ struct Metric<true> {
             double cz = gap(q.z, __int_as_float(lo.z), __int_as_float(hi.z));
             s = __dadd_rn(s, __dmul_rn(cz, cz));
         }
-        return s;
+        return bits(s);
     }
     // A point outside the box in dimension j differs from q by more than the
     // gap m_j to that face; rounding is monotone, so its ranking value is at
     // least fl(m_j^2).  Stop iff fl(m_j^2) > thr in every dimension.
-    __device__ static bool side_ok(double q, float lo, float hi, double thr)
+    __device__ static bool side_ok(double q, float lo, float hi, D thr)
     {
-        double a = __dsub_rn(q, (double)lo), b = __dsub_rn((double)hi, q);
-        double m = a < b ? a : b;
-        return m >= 0.0 && __dmul_rn(m, m) > thr;
+        const double a = __dsub_rn(q, (double)lo), b = __dsub_rn((double)hi, q);
+        const D ab = bits(a), bb = bits(b);
+        if (ab < 0 || bb < 0) return false; // outside the box (or -0): no stop
+        const double m = ab < bb ? a : b;
+        return bits(__dmul_rn(m, m)) > thr;
     }
     template <int DIM>
     __device__ static bool inside(const Q &q, int4 lo, int4 hi, D thr)
@@ -151,6 +160,46 @@ struct Metric<true> {
         if (DIM == 3 && !side_ok(q.z, __int_as_float(lo.z), __int_as_float(hi.z), thr)) return false;
         return true;
     }
+};
+
+// fp32 threshold for the candidate filter of float trees: the fp32 estimate
+// of D carries a relative error below 2^-20 (two roundings of each
+// difference and square, three of the sum), so a candidate with D <= thr
+// always has estimate <= thr * (1 + 2^-18), rounded up.  thr: bit pattern.
+__device__ __forceinline__ float thr_float_f(long long thr)
+{
+    if (thr >= 0x7ff0000000000000ll) return __int_as_float(0x7f800000);
+    return __fmul_ru(__double2float_ru(__longlong_as_double(thr)), 1.0f + 1.0f / 262144.0f);
+}
+
+// Candidate filter before the exact distance: nothing for integer trees; for
+// float trees an fp32 estimate against the margin threshold above, which
+// skips the fp64 evaluation of candidates that cannot enter the list.
+template <bool FLOAT>
+struct Prefilter {
+    __device__ explicit Prefilter(int4) {}
+    template <int DIM>
+    __device__ bool pass(int4) const { return true; }
+    __device__ void update(long long) {}
+};
+template <>
+struct Prefilter<true> {
+    float x, y, z, thr;
+    __device__ explicit Prefilter(int4 q)
+    {
+        x = __int_as_float(q.x);
+        y = __int_as_float(q.y);
+        z = __int_as_float(q.z);
+        thr = __int_as_float(0x7f800000);
+    }
+    template <int DIM>
+    __device__ bool pass(int4 p) const
+    {
+        const float ex = x - __int_as_float(p.x), ey = y - __int_as_float(p.y);
+        const float ez = DIM == 3 ? z - __int_as_float(p.z) : 0.f;
+        return fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= thr;
+    }
+    __device__ void update(long long kth) { thr = thr_float_f(kth); }
 };
 
 // Insert (d, id) into the sorted k-best list (the caller checked that it
@@ -177,7 +226,7 @@ __device__ __forceinline__ void kb_insert(D (&bd)[K], int (&bi)[K], D d, int id)
 
 template <int DIM, int K, bool FLOAT>
 __device__ __forceinline__ void scan_leaf(const TreeView &t, int leaf, int self,
-                                          const typename Metric<FLOAT>::Q &q,
+                                          const typename Metric<FLOAT>::Q &q, Prefilter<FLOAT> &pf,
                                           typename Metric<FLOAT>::D (&bd)[K], int (&bi)[K])
 {
     typedef Metric<FLOAT> M;
@@ -185,8 +234,12 @@ __device__ __forceinline__ void scan_leaf(const TreeView &t, int leaf, int self,
     for (int p = lo; p < hi; ++p) {
         if (p == self) continue; // all-points mode: the query itself (by position = by id)
         const int4 c = __ldg(t.pts + p);
+        if (!pf.template pass<DIM>(c)) continue;
         const typename M::D d = M::template dist<DIM>(q, c);
-        if (d < bd[K - 1] || (d == bd[K - 1] && c.w < bi[K - 1])) kb_insert<K>(bd, bi, d, c.w);
+        if (d < bd[K - 1] || (d == bd[K - 1] && c.w < bi[K - 1])) {
+            kb_insert<K>(bd, bi, d, c.w);
+            pf.update(bd[K - 1]);
+        }
     }
 }
 
@@ -220,7 +273,7 @@ __device__ __forceinline__ bool cell_inside(int4 qp, uint3 shift, int pbit, long
 // searchDown (Algorithm 2) from node v whose box distance is dv.
 template <int DIM, int K, bool FLOAT>
 __device__ __forceinline__ void search_down(const TreeView &t, int v, typename Metric<FLOAT>::D dv,
-                                            int self, const typename Metric<FLOAT>::Q &q,
+                                            int self, const typename Metric<FLOAT>::Q &q, Prefilter<FLOAT> &pf,
                                             typename Metric<FLOAT>::D (&bd)[K], int (&bi)[K],
                                             u32 *status)
 {
@@ -237,7 +290,7 @@ __device__ __forceinline__ void search_down(const TreeView &t, int v, typename M
         const int u = sn[sp];
         if (sd[sp] > bd[K - 1]) continue; // pruned by the (possibly shrunk) k-th distance
         if (u < 0) {
-            scan_leaf<DIM, K, FLOAT>(t, ~u, self, q, bd, bi);
+            scan_leaf<DIM, K, FLOAT>(t, ~u, self, q, pf, bd, bi);
             continue;
         }
         const int2 ch = __ldg(t.ichild + u);
@@ -296,6 +349,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
         row = qp.w;
     }
     const typename M::Q q = M::make(qp);
+    Prefilter<FLOAT> pf(qp);
     const u64 *qkeys = a.allpts ? t.keys : a.qkey;
 
     if (t.n > 0) {
@@ -316,7 +370,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
             if (ok) {
                 int4 lo, hi;
                 node_box(t, v, lo, hi);
-                search_down<DIM, K, FLOAT>(t, v, M::template boxd<DIM>(q, lo, hi), self, q, bd, bi, status);
+                search_down<DIM, K, FLOAT>(t, v, M::template boxd<DIM>(q, lo, hi), self, q, pf, bd, bi, status);
             }
         } else {
             int leaf;
@@ -333,7 +387,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
                 leaf = ~v;
             }
             // searchUp (Algorithm 3)
-            scan_leaf<DIM, K, FLOAT>(t, leaf, self, q, bd, bi);
+            scan_leaf<DIM, K, FLOAT>(t, leaf, self, q, pf, bd, bi);
             int node = ~leaf;
             int par = __ldg(t.lparent + leaf);
             while (par >= 0 && __ldg(t.ibit + par) < t.cloud_bit) {
@@ -350,7 +404,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
                 const int sib = ch.x == node ? ch.y : ch.x;
                 node_box(t, sib, lo, hi);
                 const D ds = M::template boxd<DIM>(q, lo, hi);
-                if (ds <= bd[K - 1]) search_down<DIM, K, FLOAT>(t, sib, ds, self, q, bd, bi, status);
+                if (ds <= bd[K - 1]) search_down<DIM, K, FLOAT>(t, sib, ds, self, q, pf, bd, bi, status);
                 node = par;
                 par = __ldg(t.iparent + par);
             }
@@ -367,7 +421,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
             float *od = (float *)a.out_dist + row * k;
 #pragma unroll
             for (int j = 0; j < K; ++j)
-                if (j < k) od[j] = bd[j] < M::inf() ? (float)sqrt((double)bd[j]) : __int_as_float(0x7f800000);
+                if (j < k) od[j] = bd[j] < M::inf() ? M::out_dist(bd[j]) : __int_as_float(0x7f800000);
         } else {
             long long *od = (long long *)a.out_dist + row * k;
 #pragma unroll

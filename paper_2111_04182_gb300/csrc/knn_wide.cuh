@@ -10,8 +10,11 @@
 // climb, search siblings down with a box test against the k-th distance --
 // is the one of the one-thread-per-query kernel, executed in lockstep by the
 // warp (every branch depends only on warp-uniform values); the DFS stack is
-// spread over the lanes as well.  Leaves are scanned 32 points at a time,
-// one point per lane.
+// a per-warp shared-memory array that every lane writes identically.
+// Leaves are scanned 32 points at a time, one point per lane; for k <= 64 a
+// subtree of at most WIDE_SMALL_SUBTREE points is scanned whole (its points
+// are contiguous in sorted order) instead of descending into it, which
+// trades box pruning for full-width rounds and fewer node visits.
 //
 // Filling: until k candidates have been seen the k-th distance is infinite
 // and every candidate enters, so the first candidates are appended unsorted
@@ -20,15 +23,25 @@
 // that beats the k-th best is inserted by the warp: its rank comes from one
 // ballot per register, and the slots from the rank up move up by one place
 // (a shuffle, lane 0 taking lane 31 of the register below), which drops the
-// old k-th best off the top.
+// old k-th best off the top.  For k > 64 (four registers) such single
+// insertions cost more than batching: candidates that beat the k-th best are
+// appended to a per-warp pending block of 32 and merged when it holds
+// WIDE_FLUSH or more after a leaf, or would overflow -- the block is sorted
+// (bitonic), then, from the top register down, the larger half of (register,
+// reversed block) stays and the smaller half moves on (Batcher's bitonic
+// split), stopping at the first register the block lies entirely above.
+// Until a merge the threshold is the stale, larger k-th distance, which only
+// admits more candidates and prunes less; the answer is the same.
 #pragma once
 
 #include "knn_impl.cuh"
 
 namespace zdk {
 
-constexpr int WIDE_WARPS = 4;      // queries in flight per block
-constexpr int WIDE_STACK_REGS = 3; // DFS stack: 96 entries spread over the lanes
+constexpr int WIDE_WARPS = 4;          // queries in flight per block
+constexpr int WIDE_STACK = 96;         // DFS stack entries per warp
+constexpr int WIDE_SMALL_SUBTREE = 128; // k <= 64: subtrees scanned whole
+constexpr int WIDE_FLUSH = 16;         // k > 64: pending candidates merged after a leaf
 constexpr unsigned WFULL = 0xffffffffu;
 
 template <typename D>
@@ -94,6 +107,7 @@ struct WideQuery {
 
     const TreeView &t;
     typename M::Q q;
+    Prefilter<FLOAT> pf; // float trees: fp32 candidate filter
     int self;  // sorted position to skip (all-points), else -1
     int lane;
     int k, off; // k, and the slot of the best (32 R - k)
@@ -105,10 +119,16 @@ struct WideQuery {
     int count; // entries appended while filling
     D *bufd;   // this warp's fill buffer [32 R]
     int *bufi;
+    D *pend_d; // this warp's pending block [32] (R >= 4)
+    int *pend_i;
+    int pc;     // pending candidates
+    int *stk_n; // this warp's DFS stack [WIDE_STACK]
+    D *stk_d;
 
-    __device__ WideQuery(const TreeView &t_, int k_, int lane_, D *bd, int *bi)
-        : t(t_), self(-1), lane(lane_), k(k_), off(32 * R - k_), td(M::inf()),
-          ti(INT_MAX), filling(true), count(0), bufd(bd), bufi(bi)
+    __device__ WideQuery(const TreeView &t_, int k_, int lane_, D *bd, int *bi, D *pd, int *pi, int *sn, D *sd)
+        : t(t_), pf(make_int4(0, 0, 0, 0)), self(-1), lane(lane_), k(k_), off(32 * R - k_), td(M::inf()),
+          ti(INT_MAX), filling(true),
+          count(0), bufd(bd), bufi(bi), pend_d(pd), pend_i(pi), pc(0), stk_n(sn), stk_d(sd)
     {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -121,6 +141,7 @@ struct WideQuery {
     {
         td = __shfl_sync(WFULL, d[R - 1], 31);
         ti = __shfl_sync(WFULL, id[R - 1], 31);
+        pf.update(td);
     }
 
     // Move the fill buffer into slots off .. off + count - 1 (sentinels
@@ -171,9 +192,50 @@ struct WideQuery {
         refresh_kth();
     }
 
+    // Merge the pending block into the list (R >= 4).
+    __device__ __forceinline__ void merge_pending()
+    {
+        __syncwarp();
+        D xd[1];
+        int xi[1];
+        xd[0] = lane < pc ? pend_d[lane] : M::inf();
+        xi[0] = lane < pc ? pend_i[lane] : INT_MAX;
+        __syncwarp();
+        pc = 0;
+        wide_sort<2, 1>(xd, xi, lane);
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) {
+            const D yd = __shfl_sync(WFULL, xd[0], 31 - lane);
+            const int yi = __shfl_sync(WFULL, xi[0], 31 - lane);
+            const bool sw = wkey_lt(yd, yi, d[r], id[r]);
+            const bool any = __any_sync(WFULL, sw);
+            if (r < R - 1) { // the larger half, sorted, is register r + 1
+                D hd[1] = {sw ? d[r] : yd};
+                int hn[1] = {sw ? id[r] : yi};
+                wide_stage<32, 16, 1>(hd, hn, lane);
+                d[r + 1] = hd[0];
+                id[r + 1] = hn[0];
+            }
+            if (!any) break; // the block lay above register r: the rest is unchanged
+            xd[0] = sw ? yd : d[r];
+            xi[0] = sw ? yi : id[r];
+            wide_stage<32, 16, 1>(xd, xi, lane);
+            if (r == 0) {
+                d[0] = xd[0];
+                id[0] = xi[0];
+            }
+        }
+        refresh_kth();
+    }
+
     __device__ __forceinline__ void scan_leaf(int leaf)
     {
-        const int lo = __ldg(t.leaf_lo + leaf), hi = __ldg(t.leaf_lo + leaf + 1);
+        scan_range(__ldg(t.leaf_lo + leaf), __ldg(t.leaf_lo + leaf + 1));
+    }
+
+    // The candidates at sorted positions [lo, hi), 32 per round.
+    __device__ __forceinline__ void scan_range(int lo, int hi)
+    {
         for (int base = lo; base < hi; base += 32) {
             const int p = base + lane;
             D cd = M::inf();
@@ -181,9 +243,11 @@ struct WideQuery {
             bool ok = false;
             if (p < hi && p != self) {
                 const int4 c = __ldg(t.pts + p);
-                cd = M::template dist<DIM>(q, c);
-                ci = c.w;
-                ok = wkey_lt(cd, ci, td, ti);
+                if (pf.template pass<DIM>(c)) {
+                    cd = M::template dist<DIM>(q, c);
+                    ci = c.w;
+                    ok = wkey_lt(cd, ci, td, ti);
+                }
             }
             unsigned mask = __ballot_sync(WFULL, ok);
             if (filling) {
@@ -199,6 +263,23 @@ struct WideQuery {
                 mask = __ballot_sync(WFULL, ok && rank >= placed);
                 if (count >= k || mask) finish_fill();
             }
+            if (R >= 4 && mask) {
+                bool acc = (mask >> lane) & 1;
+                int n = __popc(mask);
+                if (pc + n > 32) {
+                    merge_pending();
+                    acc = acc && wkey_lt(cd, ci, td, ti);
+                    mask = __ballot_sync(WFULL, acc);
+                    n = __popc(mask);
+                }
+                const int rank = __popc(mask & ((1u << lane) - 1u));
+                if (acc) {
+                    pend_d[pc + rank] = cd;
+                    pend_i[pc + rank] = ci;
+                }
+                pc += n;
+                mask = 0;
+            }
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
@@ -207,47 +288,33 @@ struct WideQuery {
                 if (wkey_lt(xd, xi, td, ti)) insert(xd, xi);
             }
         }
+        if (R >= 4 && pc >= WIDE_FLUSH) merge_pending();
     }
 
-    // searchDown (Algorithm 2) from node v whose box distance is dv.
+    // searchDown (Algorithm 2) from node v whose box distance is dv.  Every
+    // lane pushes and pops the same entries; the __syncwarp after a pop keeps
+    // a lane from overwriting the entry before all lanes have read it.
     __device__ __forceinline__ bool search_down(int v, D dv, u32 *status)
     {
-        int sn[WIDE_STACK_REGS];
-        D sd[WIDE_STACK_REGS];
-#pragma unroll
-        for (int r = 0; r < WIDE_STACK_REGS; ++r) {
-            sn[r] = 0;
-            sd[r] = D(0);
-        }
-        int sp = 0;
-        auto push = [&](int u, D du) {
-            const int reg = sp >> 5, ln = sp & 31;
-#pragma unroll
-            for (int r = 0; r < WIDE_STACK_REGS; ++r)
-                if (r == reg && lane == ln) {
-                    sn[r] = u;
-                    sd[r] = du;
-                }
-            ++sp;
-        };
-        push(v, dv);
+        stk_n[0] = v;
+        stk_d[0] = dv;
+        int sp = 1;
         while (sp > 0) {
             --sp;
-            const int reg = sp >> 5, ln = sp & 31;
-            int u0 = sn[0];
-            D d0 = sd[0];
-#pragma unroll
-            for (int r = 1; r < WIDE_STACK_REGS; ++r)
-                if (r == reg) {
-                    u0 = sn[r];
-                    d0 = sd[r];
-                }
-            const int u = __shfl_sync(WFULL, u0, ln);
-            const D du = __shfl_sync(WFULL, d0, ln);
+            const int u = stk_n[sp];
+            const D du = stk_d[sp];
+            __syncwarp();
             if (du > td) continue; // pruned by the (possibly shrunk) k-th distance
             if (u < 0) {
                 scan_leaf(~u);
                 continue;
+            }
+            if (R == 2) {
+                const int2 rg = __ldg(t.irange + u);
+                if (rg.y - rg.x <= WIDE_SMALL_SUBTREE) {
+                    scan_range(rg.x, rg.y);
+                    continue;
+                }
             }
             const int2 ch = __ldg(t.ichild + u);
             int4 al, ah, bl, bh;
@@ -257,12 +324,20 @@ struct WideQuery {
             const D db = M::template boxd<DIM>(q, bl, bh);
             const int nf = da <= db ? ch.y : ch.x, nn = da <= db ? ch.x : ch.y;
             const D df = da <= db ? db : da, dn = da <= db ? da : db;
-            if (sp + 2 > 32 * WIDE_STACK_REGS) {
+            if (sp + 2 > WIDE_STACK) {
                 if (lane == 0) set_status(status, ZD_ERR_CUDA);
                 return false;
             }
-            if (df <= td) push(nf, df);
-            if (dn <= td) push(nn, dn);
+            if (df <= td) {
+                stk_n[sp] = nf;
+                stk_d[sp] = df;
+                ++sp;
+            }
+            if (dn <= td) {
+                stk_n[sp] = nn;
+                stk_d[sp] = dn;
+                ++sp;
+            }
         }
         return true;
     }
@@ -273,8 +348,13 @@ __global__ void __launch_bounds__(32 * WIDE_WARPS, 4) k_knn_wide(KnnArgs a, u32 
 {
     typedef Metric<FLOAT> M;
     typedef typename M::D D;
+    constexpr int PEND = R >= 4 ? 32 : 1;
     __shared__ D s_bufd[WIDE_WARPS][32 * R];
     __shared__ int s_bufi[WIDE_WARPS][32 * R];
+    __shared__ D s_pd[WIDE_WARPS][PEND];
+    __shared__ int s_pi[WIDE_WARPS][PEND];
+    __shared__ D s_sd[WIDE_WARPS][WIDE_STACK];
+    __shared__ int s_sn[WIDE_WARPS][WIDE_STACK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const TreeView &t = a.t;
     const int nl = __ldg(t.meta);
@@ -283,7 +363,8 @@ __global__ void __launch_bounds__(32 * WIDE_WARPS, 4) k_knn_wide(KnnArgs a, u32 
     for (int64_t qi = (int64_t)blockIdx.x * WIDE_WARPS + warp; qi < a.m;
          qi += (int64_t)gridDim.x * WIDE_WARPS) {
         __syncwarp();
-        WideQuery<DIM, R, FLOAT> w(t, a.k, lane, s_bufd[warp], s_bufi[warp]);
+        WideQuery<DIM, R, FLOAT> w(t, a.k, lane, s_bufd[warp], s_bufi[warp], s_pd[warp], s_pi[warp], s_sn[warp],
+                                   s_sd[warp]);
         int4 qp;
         int64_t row;
         if (a.allpts) {
@@ -296,6 +377,7 @@ __global__ void __launch_bounds__(32 * WIDE_WARPS, 4) k_knn_wide(KnnArgs a, u32 
             row = qp.w;
         }
         w.q = M::make(qp);
+        w.pf = Prefilter<FLOAT>(qp);
 
         bool ok = true;
         if (t.n > 0) {
@@ -355,6 +437,7 @@ __global__ void __launch_bounds__(32 * WIDE_WARPS, 4) k_knn_wide(KnnArgs a, u32 
             }
         }
         if (w.filling) w.finish_fill();
+        if (R >= 4 && w.pc > 0) w.merge_pending();
 
         const int k = a.k;
         int32_t *oi = a.out_idx + row * k;
@@ -370,7 +453,7 @@ __global__ void __launch_bounds__(32 * WIDE_WARPS, 4) k_knn_wide(KnnArgs a, u32 
                 if (e < 0) continue;
                 if (FLOAT)
                     ((float *)a.out_dist)[row * k + e] =
-                        w.d[r] < M::inf() ? (float)sqrt((double)w.d[r]) : __int_as_float(0x7f800000);
+                        w.d[r] < M::inf() ? M::out_dist(w.d[r]) : __int_as_float(0x7f800000);
                 else
                     ((long long *)a.out_dist)[row * k + e] = (long long)w.d[r];
             }
