@@ -610,13 +610,14 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
     } else {
         a.n_groups = (m + 31) / 32;
     }
-    if (t->is_float) return launch_knn_group_f32(a, s);
-    // packed keys: the ids need idb bits
-    a.idb = std::max(1, ceil_log2(t->cloud_off ? t->max_cloud : t->next_id));
+    // queries handed back to the exact one-thread kernel
     Scratch<int> fix(mem, (size_t)(allpts ? t->n : m) + 1);
     if (!fix.p) return ZD_ERR_OOM;
     a.fix_count = fix.p;
     a.fix_list = fix.p + 1;
+    if (t->is_float) return launch_knn_group_f32(a, s);
+    // packed keys: the ids need idb bits
+    a.idb = std::max(1, ceil_log2(t->cloud_off ? t->max_cloud : t->next_id));
     return launch_knn_group_i32(a, s);
 }
 

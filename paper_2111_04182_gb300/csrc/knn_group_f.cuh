@@ -4,20 +4,33 @@
 //
 // Neighbours are ranked exactly as the oracle ranks them: by (D, id) with
 // D = ((dx*dx + dy*dy) + dz*dz) in fp64, dx = (double)q.x - (double)p.x, no
-// contraction.  Each lane keeps its k best as (D, id) pairs, D held as the
-// int64 bit pattern of the double (ordered like the value) so that list
-// comparisons avoid the fp64 pipe.  Candidates are
-// first filtered in fp32: the fp32 estimate of D carries a relative error
-// below 2^-20 (two roundings of each difference and square, three of the
-// sum), so a candidate with D <= thr always has estimate <= thr * (1 + 2^-18)
-// rounded up; only candidates passing that test compute D in fp64.  The same
-// margin guards the fp32 box tests.  The climb tests the tight box in fp64
-// (the float cell of a node is not a box in coordinates).
+// contraction.  GB300's fp64 pipe is narrow, so the traversal never touches
+// it: each lane ranks candidates by the fp32 estimate
+//   est = fma(x, x, fma(y, y, z*z)),  x = fl32(q.x - p.x), ...
+// whose relative error against D is below 2^-20 (one rounding of each
+// difference, three roundings in the sum, D itself within 2^-50), and keeps
+// the K + FSLACK smallest (est, sorted position) in registers as packed u64
+// keys.  Let eK be the K-th smallest estimate seen.  Then K candidates have
+// D <= eK (1 + 2^-20), so every true neighbour has est <= B = eK (1 + 2^-18)
+// -- the band.  Candidates and boxes are filtered against
+// thr = eK (1 + 2^-17) rounded up (which also covers the box estimate's own
+// error), and the climb stops on a lower bound of any outside point's
+// estimate, so every candidate in the final band is examined.  A candidate
+// that passes the filter but is not kept (or is evicted later) records its
+// estimate in ovf; if ovf <= B at the end, the band overflowed the list
+// (near-ties, duplicates) and the query is handed to the exact
+// one-thread-per-query kernel.  Otherwise the band lies in the list: its
+// entries get their exact D (the only fp64 arithmetic, <= K + FSLACK
+// evaluations per query), are sorted by (D, id), and the first k are the
+// answer.  Coordinates are assumed below ~1e19 in magnitude so that the fp32
+// squares do not overflow; a tiny absolute slack (1e-36) covers underflow.
 #pragma once
 
 #include "knn_group.cuh"
 
 namespace zdk {
+
+constexpr int FSLACK = 2; // list entries kept beyond K
 
 struct GroupCtxF {
     float fx, fy, fz;    // the query
@@ -38,47 +51,11 @@ __device__ __forceinline__ double exact_d2(const GroupCtxF &c, float4 p)
     return s;
 }
 
-template <int DIM, int K>
-__device__ __forceinline__ void accept_f(int p, float4 pt, const GroupCtxF &c, long long (&bd)[K], int (&bi)[K],
-                                         float &thr_f)
-{
-    if (p == c.self) return;
-    const long long d = __double_as_longlong(exact_d2<DIM>(c, pt));
-    const int id = __float_as_int(pt.w);
-    if (d < bd[K - 1] || (d == bd[K - 1] && id < bi[K - 1])) {
-        kb_insert<K>(bd, bi, d, id);
-        thr_f = thr_float_f(bd[K - 1]);
-    }
-}
-
 template <int DIM>
 __device__ __forceinline__ float est_d2(const GroupCtxF &c, float4 p)
 {
     const float x = c.fx - p.x, y = c.fy - p.y, z = DIM == 3 ? c.fz - p.z : 0.f;
     return fmaf(x, x, fmaf(y, y, z * z));
-}
-
-template <int DIM, int K>
-__device__ __forceinline__ void group_scan_ff(const TreeView &t, int a, int b, const GroupCtxF &c,
-                                              long long (&bd)[K], int (&bi)[K], float &thr_f)
-{
-    const float4 *pts = (const float4 *)t.pts;
-    int p = a;
-    for (; p + 1 < b; p += 2) {
-        const float4 u = __ldg(pts + p), v = __ldg(pts + p + 1);
-        const bool pu = c.live && est_d2<DIM>(c, u) <= thr_f, pv = c.live && est_d2<DIM>(c, v) <= thr_f;
-        if (__any_sync(0xffffffffu, pu || pv)) {
-            if (pu) accept_f<DIM, K>(p, u, c, bd, bi, thr_f);
-            if (pv) accept_f<DIM, K>(p + 1, v, c, bd, bi, thr_f);
-        }
-    }
-    if (p < b) {
-        const float4 u = __ldg(pts + p);
-        const bool pu = c.live && est_d2<DIM>(c, u) <= thr_f;
-        if (__any_sync(0xffffffffu, pu)) {
-            if (pu) accept_f<DIM, K>(p, u, c, bd, bi, thr_f);
-        }
-    }
 }
 
 template <int DIM>
@@ -93,10 +70,79 @@ __device__ __forceinline__ float box_est(const GroupCtxF &c, float4 lo, float4 h
     return fmaf(cx, cx, cy * cy);
 }
 
+// Estimate of a packed key (empty slots read as NaN, which no test accepts).
+__device__ __forceinline__ float key_est(u64 key) { return __uint_as_float((unsigned)(key >> 32)); }
+
+// Filter threshold from the K-th estimate: eK (1 + 2^-17) + 1e-36, rounded up.
+__device__ __forceinline__ float filter_thr(float eK)
+{
+    if (!(eK < __int_as_float(0x7f800000))) return __int_as_float(0x7f800000);
+    return __fadd_ru(__fmul_ru(eK, 1.0f + 1.0f / 131072.0f), 1e-36f);
+}
+
+// The band bound B: eK (1 + 2^-18) + 1e-36, rounded up.
+__device__ __forceinline__ float band_of(float eK)
+{
+    if (!(eK < __int_as_float(0x7f800000))) return __int_as_float(0x7f800000);
+    return __fadd_ru(__fmul_ru(eK, 1.0f + 1.0f / 262144.0f), 1e-36f);
+}
+
+template <int K>
+struct EstList {
+    static constexpr int KP = K + FSLACK;
+    u64 key[KP]; // (est bits << 32) | sorted position, ascending
+    float ovf;   // smallest estimate that passed the filter but is not kept
+    float thr;   // filter / pruning threshold
+
+    __device__ void init()
+    {
+#pragma unroll
+        for (int j = 0; j < KP; ++j) key[j] = ~0ull;
+        ovf = __int_as_float(0x7f800000);
+        thr = ovf;
+    }
+    __device__ __forceinline__ void offer(float est, int p)
+    {
+        const u64 ck = ((u64)__float_as_uint(est) << 32) | (u64)(unsigned)p;
+        if (ck < key[KP - 1]) {
+            ovf = fminf(ovf, key_est(key[KP - 1])); // NaN (empty slot) leaves ovf alone
+            key_insert<KP>(key, ck);
+            thr = filter_thr(key_est(key[K - 1]));
+        } else {
+            ovf = fminf(ovf, est);
+        }
+    }
+};
+
+// Scan sorted positions [a, b) for every lane, two candidates per step.
+template <int DIM, int K>
+__device__ __forceinline__ void group_scan_ff(const TreeView &t, int a, int b, const GroupCtxF &c, EstList<K> &L)
+{
+    const float4 *pts = (const float4 *)t.pts;
+    int p = a;
+    for (; p + 1 < b; p += 2) {
+        const float4 u = __ldg(pts + p), v = __ldg(pts + p + 1);
+        const float eu = est_d2<DIM>(c, u), ev = est_d2<DIM>(c, v);
+        const bool pu = c.live && eu <= L.thr && p != c.self;
+        const bool pv = c.live && ev <= L.thr && p + 1 != c.self;
+        if (__any_sync(0xffffffffu, pu || pv)) {
+            if (pu) L.offer(eu, p);
+            if (pv && ev <= L.thr) L.offer(ev, p + 1);
+        }
+    }
+    if (p < b) {
+        const float4 u = __ldg(pts + p);
+        const float eu = est_d2<DIM>(c, u);
+        const bool pu = c.live && eu <= L.thr && p != c.self;
+        if (__any_sync(0xffffffffu, pu)) {
+            if (pu) L.offer(eu, p);
+        }
+    }
+}
+
 template <int DIM, int K>
 __device__ __forceinline__ void group_search_ff(const TreeView &t, int start, int l0, int l1, u64 mid_key,
-                                                int *stack, const GroupCtxF &c, long long (&bd)[K], int (&bi)[K],
-                                                float &thr_f, u32 *status)
+                                                int *stack, const GroupCtxF &c, EstList<K> &L, u32 *status)
 {
     const int lane = threadIdx.x & 31;
     if (lane == 0) stack[0] = start;
@@ -107,10 +153,10 @@ __device__ __forceinline__ void group_search_ff(const TreeView &t, int start, in
         __syncwarp();
         if (v < 0 && ~v >= l0 && ~v <= l1) continue; // scanned already
         const float4 *b = (const float4 *)(v < 0 ? t.lbox + 2 * (~v) : t.ibox + 2 * v);
-        const bool need = c.live && box_est<DIM>(c, __ldg(b), __ldg(b + 1)) <= thr_f;
+        const bool need = c.live && box_est<DIM>(c, __ldg(b), __ldg(b + 1)) <= L.thr;
         if (!__any_sync(0xffffffffu, need)) continue;
         if (v < 0) {
-            group_scan_ff<DIM, K>(t, __ldg(t.leaf_lo + ~v), __ldg(t.leaf_lo + ~v + 1), c, bd, bi, thr_f);
+            group_scan_ff<DIM, K>(t, __ldg(t.leaf_lo + ~v), __ldg(t.leaf_lo + ~v + 1), c, L);
             continue;
         }
         const int2 ch = __ldg(t.ichild + v);
@@ -126,6 +172,18 @@ __device__ __forceinline__ void group_search_ff(const TreeView &t, int start, in
         sp += 2;
         __syncwarp();
     }
+}
+
+// Climb test on one axis: every point outside [lo, hi] along it has an
+// estimate above thr.  m <= (true gap)(1 + 2^-24); ml = m (1 - 2^-22) rounded
+// down is at most the true gap g, and an outside point's estimate is at least
+// g^2 (1 - 2^-21) >= ml^2 (1 - 2^-20) with both products rounded down.
+__device__ __forceinline__ bool axis_clear_f(float q, float lo, float hi, float thr)
+{
+    const float m = fminf(q - lo, hi - q);
+    if (!(m >= 0.f)) return false;
+    const float ml = __fmul_rd(m, 1.0f - 1.0f / 4194304.0f);
+    return __fmul_rd(__fmul_rd(ml, ml), 1.0f - 1.0f / 1048576.0f) > thr;
 }
 
 template <int DIM, int K>
@@ -160,14 +218,8 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group_f(KnnArgs a, u32 *sta
     c.dz = (double)c.fz;
     c.self = allpts && c.live ? qi : -1;
     const u64 qkey = allpts ? __ldg(t.keys + qs) : __ldg(a.qkey + qs);
-    long long bd[K];
-    int bi[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        bd[j] = M::inf();
-        bi[j] = INT_MAX;
-    }
-    float thr_f = thr_float_f(M::inf());
+    EstList<K> L;
+    L.init();
 
     if (t.n > 0) {
         // 1. start leaves (consecutive, since the queries are sorted)
@@ -190,24 +242,26 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group_f(KnnArgs a, u32 *sta
         }
         if (cloud_ok) {
             const int P0 = __ldg(t.leaf_lo + l0), P1 = __ldg(t.leaf_lo + l1 + 1);
-            group_scan_ff<DIM, K>(t, P0, P1, c, bd, bi, thr_f);
+            group_scan_ff<DIM, K>(t, P0, P1, c, L);
             // 2. lowest common ancestor
             int C = ~l0;
             while (node_hi_pos(t, C) < P1) C = node_parent(t, C);
             const u64 mid_key = __shfl_sync(0xffffffffu, qkey, (gend - 1 - g0) >> 1);
-            group_search_ff<DIM, K>(t, C, l0, l1, mid_key, stack, c, bd, bi, thr_f, status);
-            // 3. climb: stop once every lane's ball is inside the node's tight box
+            group_search_ff<DIM, K>(t, C, l0, l1, mid_key, stack, c, L, status);
+            // 3. climb: stop once no lane's band can reach outside the node's tight box
             int node = C;
             int par = node_parent(t, C);
-            const M::Q q = {c.dx, c.dy, c.dz};
             while (par >= 0 && __ldg(t.ibit + par) < t.cloud_bit) {
-                int4 lo, hi;
-                node_box(t, node, lo, hi);
-                const bool inside = !c.live || M::template inside<DIM>(q, lo, hi, bd[K - 1]);
+                bool inside = true;
+                if (c.live) {
+                    const float4 *b = (const float4 *)(node < 0 ? t.lbox + 2 * (~node) : t.ibox + 2 * node);
+                    const float4 lo = __ldg(b), hi = __ldg(b + 1);
+                    inside = axis_clear_f(c.fx, lo.x, hi.x, L.thr) && axis_clear_f(c.fy, lo.y, hi.y, L.thr) &&
+                             (DIM == 2 || axis_clear_f(c.fz, lo.z, hi.z, L.thr));
+                }
                 if (__all_sync(0xffffffffu, inside)) break;
                 const int2 ch = __ldg(t.ichild + par);
-                group_search_ff<DIM, K>(t, ch.x == node ? ch.y : ch.x, l0, l1, mid_key, stack, c, bd, bi, thr_f,
-                                        status);
+                group_search_ff<DIM, K>(t, ch.x == node ? ch.y : ch.x, l0, l1, mid_key, stack, c, L, status);
                 node = par;
                 par = __ldg(t.iparent + par);
             }
@@ -215,6 +269,29 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group_f(KnnArgs a, u32 *sta
     }
     (void)lane;
     if (!c.live) return;
+    // 4. the band must lie in the list, else the exact kernel takes the query
+    if (L.ovf <= band_of(key_est(L.key[K - 1]))) {
+        const int slot = atomicAdd(a.fix_count, 1);
+        a.fix_list[slot] = qi;
+        return;
+    }
+    // 5. exact D of the kept candidates, sorted by (D, id)
+    constexpr int KP = EstList<K>::KP;
+    long long ed[KP];
+    int eid[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+        ed[j] = M::inf();
+        eid[j] = INT_MAX;
+    }
+    const float4 *pts = (const float4 *)t.pts;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+        if (L.key[j] != ~0ull) {
+            const float4 pt = __ldg(pts + (int)(unsigned)(L.key[j] & 0xffffffffu));
+            kb_insert<KP>(ed, eid, __double_as_longlong(exact_d2<DIM>(c, pt)), __float_as_int(pt.w));
+        }
+    }
     int64_t row = qp.w;
     if (t.cloud_off && allpts) row += __ldg(t.cloud_off + (qkey >> t.cloud_bit));
     const int k = a.k;
@@ -224,9 +301,9 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group_f(KnnArgs a, u32 *sta
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         if (j < k) {
-            const bool have = bd[j] < M::inf();
-            oi[j] = have ? bi[j] : -1;
-            if (od) od[j] = have ? M::out_dist(bd[j]) : __int_as_float(0x7f800000);
+            const bool have = ed[j] < M::inf();
+            oi[j] = have ? eid[j] : -1;
+            if (od) od[j] = have ? M::out_dist(ed[j]) : __int_as_float(0x7f800000);
         }
     }
 }

@@ -189,6 +189,28 @@ def test_skewed_sets_tree_and_all_starts(zd, oracle, name):
     t.free()
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_float_knn_ties_and_duplicates(zd, oracle, mapping):
+    """Float lattice points (many exactly equal distances) with duplicated
+    points: the estimate band overflows the warp-group list and those
+    queries take the exact fallback; the answer stays the oracle's."""
+    g = np.stack(np.meshgrid(*[np.arange(18)] * 3, indexing="ij"), -1).reshape(-1, 3).astype(np.float32) * 0.25
+    pts = np.concatenate([g, g[:700], g[::5] + 0.125]).astype(np.float32)
+    t = zd.zd_build(_t(pts), 16, 21)
+    for k in (1, 6, 8, 16):
+        idx, dist = t.knn(k, mapping=mapping)
+        assert zd.zd_check() == 0
+        bi, bd = oracle.knn_brute(pts, k)
+        assert np.array_equal(idx.cpu().numpy(), bi), k
+        assert np.allclose(dist.cpu().numpy(), np.sqrt(bd), rtol=1e-6, atol=0), k
+    q = (np.random.default_rng(80).integers(0, 70, size=(3000, 3)) * 0.0625).astype(np.float32)
+    for mode in (1, 2):
+        idx, dist = t.knn(8, queries=_t(q), mode=mode, mapping=mapping)
+        bi, bd = oracle.knn_brute(pts, 8, queries=q)
+        assert np.array_equal(idx.cpu().numpy(), bi), mode
+    t.free()
+
+
 def test_float_knn_graph_three_starts(zd, oracle):
     from paper_2111_04182_gb300 import datagen
     _, b = datagen.warped_pair(np.random.default_rng(79), 10, 7000)
