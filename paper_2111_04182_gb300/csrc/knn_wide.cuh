@@ -6,9 +6,11 @@
 // e = 32 r + lane lives in register r of that lane.  The list is kept sorted
 // by (squared distance, id) over e and aligned to the end: the j-th best is
 // slot 32 R - k + j, so the k-th best is always register R - 1 of lane 31,
-// and slots below 32 R - k hold sentinels that order before every point.  The traversal -- scan the start leaf,
-// climb, search siblings down with a box test against the k-th distance --
-// is the one of the one-thread-per-query kernel, executed in lockstep by the
+// and slots below 32 R - k hold sentinels that order before every point.
+// The traversal -- scan the start leaf, climb, search siblings down with a
+// box test against the k-th distance -- is the one of the
+// one-thread-per-query kernel (float trees with its fp32 candidate filter
+// and int64-ordered fp64 values), executed in lockstep by the
 // warp (every branch depends only on warp-uniform values); the DFS stack is
 // a per-warp shared-memory array that every lane writes identically.
 // Leaves are scanned 32 points at a time, one point per lane; for k <= 64 a
@@ -38,10 +40,10 @@
 
 namespace zdk {
 
-constexpr int WIDE_WARPS = 4;          // queries in flight per block
-constexpr int WIDE_STACK = 96;         // DFS stack entries per warp
+constexpr int WIDE_WARPS = 4;           // queries in flight per block
+constexpr int WIDE_STACK = 96;          // DFS stack entries per warp
 constexpr int WIDE_SMALL_SUBTREE = 128; // k <= 64: subtrees scanned whole
-constexpr int WIDE_FLUSH = 16;         // k > 64: pending candidates merged after a leaf
+constexpr int WIDE_FLUSH = 16;          // k > 64: pending candidates merged after a leaf
 constexpr unsigned WFULL = 0xffffffffu;
 
 template <typename D>
