@@ -605,10 +605,11 @@ def bench_update_sweep(args):
     batch size (the paper's update and dynamic-query plots): a 2D tree of
     10^7 uniform points in [0, 2^20)^2, L = 16; for each batch size b an
     insert of b uniform points then a delete of those b ids (the set is
-    restored each time), and bit-based k = 1 queries in batches of m.
+    restored each time), and bit-based queries in batches of m.
     Insert and delete validate on the host (they sync), so their times are
-    whole-call latencies.  At the end the tree must equal a fresh build of
-    the original points (same sorted keys and node structure)."""
+    whole-call latencies.  Queries use k = 1, 5 and 10.  At the end the tree
+    must equal a fresh build of the original points (same sorted keys and
+    node structure)."""
     import torch
     from paper_2111_04182_gb300 import datagen, zd
     n0 = args.n
@@ -633,14 +634,15 @@ def bench_update_sweep(args):
     qs = []
     for m in (1, 100, 10_000, 1_000_000, 10_000_000):
         q = torch.from_numpy(datagen.uniform(rng, m, 2, 20)).cuda()
-        ms = []
-        for rep in range(args.warmup + max(1, args.steps // 3)):
-            a, b2 = _events(2)
-            a.record(); t.knn(1, queries=q, mode=zd.ZD_SEARCH_BIT); b2.record(); b2.synchronize()
-            if rep >= args.warmup:
-                ms.append(a.elapsed_time(b2))
-        qm = float(np.median(ms))
-        qs.append({"queries": m, "ms": qm, "s_per_query": qm / 1e3 / m})
+        for kq in (1, 5, 10):
+            ms = []
+            for rep in range(args.warmup + max(1, args.steps // 3)):
+                a, b2 = _events(2)
+                a.record(); t.knn(kq, queries=q, mode=zd.ZD_SEARCH_BIT); b2.record(); b2.synchronize()
+                if rep >= args.warmup:
+                    ms.append(a.elapsed_time(b2))
+            qm = float(np.median(ms))
+            qs.append({"queries": m, "k": kq, "ms": qm, "s_per_query": qm / 1e3 / m})
     assert zd.zd_check() == 0
     fresh = zd.zd_build(torch.from_numpy(pts).cuda(), 16, 20)
     ea, eb = t.export(), fresh.export()
