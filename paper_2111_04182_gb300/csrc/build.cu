@@ -325,6 +325,16 @@ __global__ void k_fpts(const int4 *__restrict__ pts, int64_t n, float4 *__restri
     }
 }
 
+// Atomic add with acquire-release semantics at device scope: it publishes
+// the calling thread's earlier writes and makes the writes published by
+// earlier adds to the same counter visible to it.
+__device__ __forceinline__ int atomic_add_acq_rel(int *p, int v)
+{
+    int old;
+    asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 template <bool FLOAT>
 __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
                                                const int *__restrict__ leaf_lo,
@@ -356,11 +366,11 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
             flbox[2 * j] = flo;
             flbox[2 * j + 1] = fhi;
         }
-        __threadfence();
         int p = lparent[j];
         while (p >= 0) {
-            if (atomicAdd(&counter[p], 1) == 0) break; // the sibling finishes this node
-            __threadfence();
+            // acq_rel: publishes this thread's boxes, and the second arriver
+            // sees its sibling's
+            if (atomic_add_acq_rel(&counter[p], 1) == 0) break; // the sibling finishes this node
             int2 ch = ichild[p];
             const int4 *ba = ch.x < 0 ? lbox + 2 * (~ch.x) : ibox + 2 * ch.x;
             const int4 *bb = ch.y < 0 ? lbox + 2 * (~ch.y) : ibox + 2 * ch.y;
@@ -376,7 +386,6 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
                 fibox[2 * p] = flo;
                 fibox[2 * p + 1] = fhi;
             }
-            __threadfence();
             p = iparent[p];
         }
     }
