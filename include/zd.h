@@ -178,7 +178,10 @@ int zd_morton_sort_noalloc(const uint64_t *d_keys_in, int64_t n, int key_bits, u
  * where its keys differ, leaves of at most L points, a tight bounding box per
  * node.  Float points (ZD_COORD_F32) are quantized for the keys only:
  * q = floor((x - lo_j) * s), s = (2^B - 1) / (largest extent), clamped; the
- * boxes and the search use the float values.  The point data is copied; the
+ * boxes and the search use the float values, which must be finite and at
+ * most 1e18 in magnitude (else ZD_ERR_RANGE is recorded; the same holds for
+ * float queries).  Integer coordinates outside the shifted universe record
+ * ZD_ERR_RANGE too.  The point data is copied; the
  * caller may free d_pts after the call's work is done.  *out receives the
  * handle (free with zd_free). */
 int zd_build(const zd_params *p, const zd_allocator *alloc, const void *d_pts, int64_t n,

@@ -197,13 +197,14 @@ __global__ void __launch_bounds__(256) k_encode_f32(const float *__restrict__ pt
                                                     const int64_t *__restrict__ seg_off,
                                                     int64_t n_seg, int cloud_shift,
                                                     u64 *__restrict__ keys, u32 *__restrict__ hist,
-                                                    int npasses)
+                                                    int npasses, u32 *status)
 {
     __shared__ u32 sh[MAX_PASSES * RADIX];
     if (hist)
         for (int i = threadIdx.x; i < npasses * RADIX; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const double top = (double)((1ll << B) - 1);
+    bool bad = false;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -214,6 +215,9 @@ __global__ void __launch_bounds__(256) k_encode_f32(const float *__restrict__ pt
             const double *f = frame + seg * 4;
             u64 c[3] = {0, 0, 0};
             for (int j = 0; j < DIM; ++j) {
+                // finite and at most 1e18 in magnitude (the search's fp32
+                // estimates square coordinate differences)
+                bad = bad || !(fabsf(pts[i * DIM + j]) <= 1e18f);
                 double v = floor(__dmul_rn(__dsub_rn((double)pts[i * DIM + j], f[j]), f[3]));
                 if (!(v >= 0.0)) v = 0.0;
                 if (v > top) v = top;
@@ -230,6 +234,7 @@ __global__ void __launch_bounds__(256) k_encode_f32(const float *__restrict__ pt
         for (int i = threadIdx.x; i < npasses * RADIX; i += blockDim.x)
             if (sh[i]) atomicAdd(&hist[i], sh[i]);
     }
+    if (bad) set_status(status, ZD_ERR_RANGE);
 }
 
 int launch_encode_i32(const int32_t *pts, int64_t n, int dim, int coord_bits, const uint32_t *shift,
@@ -274,10 +279,10 @@ int launch_encode_f32(const float *pts, int64_t n, int dim, int coord_bits, cons
     unsigned g = grid_for(n, 256, 152 * 16);
     if (dim == 3)
         k_encode_f32<3><<<g, 256, 0, s>>>(pts, n, coord_bits, frame, seg_off, n_seg, cloud_shift,
-                                          keys, hist, npasses);
+                                          keys, hist, npasses, status_word());
     else
         k_encode_f32<2><<<g, 256, 0, s>>>(pts, n, coord_bits, frame, seg_off, n_seg, cloud_shift,
-                                          keys, hist, npasses);
+                                          keys, hist, npasses, status_word());
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

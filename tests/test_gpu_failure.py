@@ -53,3 +53,20 @@ def test_host_checked_errors(zd):
         zd.zd_selftest_wait_timeout(0)
     t.free()
     assert zd.zd_check() == zd.ZD_OK
+
+
+def test_non_finite_float_coordinates_are_range_errors(zd):
+    pts = np.random.default_rng(3).standard_normal((1000, 3)).astype(np.float32)
+    for bad in (np.nan, np.inf, -np.inf, 3e18):
+        p = pts.copy()
+        p[17, 1] = bad
+        t = zd.zd_build(torch.from_numpy(p).cuda(), 16, 21)
+        assert zd.zd_check() == zd.ZD_ERR_RANGE, bad
+        t.free()
+    t = zd.zd_build(torch.from_numpy(pts).cuda(), 16, 21)
+    q = pts[:10].copy()
+    q[3, 0] = np.nan
+    t.knn(4, queries=torch.from_numpy(q).cuda())
+    assert zd.zd_check() == zd.ZD_ERR_RANGE
+    t.free()
+    assert zd.zd_check() == zd.ZD_OK
