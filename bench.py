@@ -70,12 +70,15 @@ def source_digest(files) -> str:
 
 KNN_SOURCES = ["paper_2111_04182_gb300/csrc/knn_impl.cuh", "paper_2111_04182_gb300/csrc/knn_group.cuh",
                "paper_2111_04182_gb300/csrc/knn_i32.cu"]
+WIDE_SOURCES = ["paper_2111_04182_gb300/csrc/knn_impl.cuh", "paper_2111_04182_gb300/csrc/knn_wide.cuh",
+                "paper_2111_04182_gb300/csrc/knn_wide.cu"]
 
 
-def profiled_traffic(kernel: str, workload: str):
+def profiled_traffic(kernel: str, workload: str, summary: str = "knn_allpoints_3d_clustered.md",
+                     sources=None):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
     None when absent or when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "knn_allpoints_3d_clustered.md")
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -83,7 +86,7 @@ def profiled_traffic(kernel: str, workload: str):
                   text)
     if not m or m.group(3) != kernel or m.group(4) != workload:
         return None
-    if m.group(2) != source_digest(KNN_SOURCES):
+    if m.group(2) != source_digest(sources or KNN_SOURCES):
         return None
     return int(m.group(1))
 
@@ -688,13 +691,16 @@ def bench_large_k(args):
     bm = float(np.median([x[0] for x in ms])); km = float(np.median([x[1] for x in ms]))
     pk, pk_src = hbm_peak()
     kb = knn_bytes_per_query(k) * n
+    traffic = (profiled_traffic("k_knn_wide", "3d-uniform-1e7-k100", "knn_wide_uniform_k100.md", WIDE_SOURCES)
+               if (n, k) == (10_000_000, 100) else None)
     return {"workload": "3d-uniform-1e7-k%d" % k, "metric": "queries/s (build + all-points k=%d)" % k,
             "value": n / ((bm + km) / 1e3), "unit": "queries/s", "build_ms": bm, "knn_ms": km,
             "knn_queries_per_s": n / (km / 1e3), "k": k, "steps": args.steps,
             "roofline": {"kernel": "k_knn_wide<3,%d,0>" % (2 if k <= 64 else 4), "bound": "hbm",
                          "achieved": kb / (km / 1e3) / 1e9,
                          "peak": pk, "peak_source": pk_src, "unit": "GB/s",
-                         "frac": kb / (km / 1e3) / 1e9 / pk, "algorithmic_bytes_per_launch": kb}}
+                         "frac": kb / (km / 1e3) / 1e9 / pk, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": kb}}
 
 
 def main():
