@@ -349,18 +349,20 @@ def run_reference(args):
     out = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": n / value * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-           "config": headline_config(n, w["k"], w["leaf_size"], w["coord_bits"], "host cores (oracle)"),
+           "config": headline_config(n, w["k"], w["leaf_size"], w["coord_bits"], "host cores (oracle)",
+                                     "n/a (host)"),
            "impl": "reference", "cpu_baseline": cb,
            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-def headline_config(n: int, k: int, L: int, B: int, parallelism: str) -> dict:
+def headline_config(n: int, k: int, L: int, B: int, parallelism: str,
+                    l2: str = "flushed between steps (256 MiB write)") -> dict:
     """The `config` object of the headline line, shared by both arms."""
     return {"workload": "3d-clustered-1e7" if n == 10_000_000 else "3d-clustered-%d" % n,
             "n": n, "dim": 3, "k": k, "leaf_size": L, "coord_bits": B, "clusters": 1000,
             "step": "build + all-points k-NN (ids and int64 d^2 written)",
-            "l2": "flushed between steps (256 MiB write)", "parallelism": parallelism}
+            "l2": l2, "parallelism": parallelism}
 
 
 def _events(n):
