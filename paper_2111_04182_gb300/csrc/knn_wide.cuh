@@ -346,7 +346,7 @@ struct WideQuery {
 };
 
 template <int DIM, int R, bool FLOAT>
-__global__ void __launch_bounds__(32 * WIDE_WARPS, 4) k_knn_wide(KnnArgs a, u32 *status)
+__global__ void __launch_bounds__(32 * WIDE_WARPS, R >= 4 ? 6 : 8) k_knn_wide(KnnArgs a, u32 *status)
 {
     typedef Metric<FLOAT> M;
     typedef typename M::D D;
