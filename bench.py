@@ -12,7 +12,7 @@ the timed region starts; L2 is flushed (256 MiB write) between steps.
 --impl reference times the CPU oracle (plain C, OpenMP over queries) on the
 host cores on a bounded sample of the same workload.  Other workloads:
 --workload 2d-uniform | dynamic | batched | differentiable | large-k | skewed |
-update-sweep.
+update-sweep | n-sweep.
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -422,7 +422,8 @@ def _events(n):
 def run_other(args, ws, rank, local):
     fn = {"2d-uniform": bench_2d, "dynamic": bench_dynamic, "batched": bench_batched,
           "differentiable": bench_differentiable, "large-k": bench_large_k,
-          "skewed": bench_skewed, "update-sweep": bench_update_sweep}.get(args.workload)
+          "skewed": bench_skewed, "update-sweep": bench_update_sweep,
+          "n-sweep": bench_n_sweep}.get(args.workload)
     if fn is None:
         raise SystemExit("unknown workload %r" % args.workload)
     out = fn(args)
@@ -712,6 +713,46 @@ def bench_update_sweep(args):
     return {"workload": "update-sweep-2d-%d" % n0, "metric": "updates/s and dynamic queries/s vs batch size",
             "value": big["batch"] / (big["insert_ms"] / 1e3), "unit": "updates/s (insert, largest batch)",
             "updates": ups, "queries": qs, "tree_equals_fresh_build": same}
+
+
+def bench_n_sweep(args):
+    """Time per point of the k-NN graph against the number of points (the
+    paper's size sweep, Sec. 5): uniform points in [0, 2^20)^3 and [0, 2^20)^2,
+    n = 10^2 .. 10^8, L = 16, k = 1, build + leaf-based all-points search.
+    Sampled rows are checked for properties any exact answer has."""
+    import torch
+    from paper_2111_04182_gb300 import datagen, zd
+    rng = np.random.default_rng(12)
+    out = []
+    for dim in (3, 2):
+        B = 21 if dim == 3 else 20
+        for n in (100, 1_000, 10_000, 100_000, 1_000_000, 10_000_000, 100_000_000):
+            pts_h = datagen.uniform(rng, n, dim, 20)
+            pts = torch.from_numpy(pts_h).cuda()
+            idx = torch.empty((n, 1), dtype=torch.int32, device="cuda")
+            d2 = torch.empty((n, 1), dtype=torch.int64, device="cuda")
+            ms = []
+            for rep in range(args.warmup + args.steps):
+                a, b = _events(2)
+                a.record(); t = zd.zd_build(pts, 16, B); t.knn(1, out=(idx, d2)); b.record(); b.synchronize()
+                t.free()
+                if rep >= args.warmup:
+                    ms.append(a.elapsed_time(b))
+            assert zd.zd_check() == 0
+            rows = rng.choice(n, min(n, 2048), replace=False)
+            r_d = torch.from_numpy(rows).cuda()
+            I, D = idx[r_d].cpu().numpy(), d2[r_d].cpu().numpy()
+            diff = pts_h[I].astype(np.int64) - pts_h[rows][:, None, :].astype(np.int64)
+            if not (np.array_equal((diff * diff).sum(-1), D) and np.all(I != rows[:, None])):
+                raise RuntimeError("n-sweep rows fail the property checks (dim %d, n %d)" % (dim, n))
+            m = float(np.median(ms))
+            out.append({"dim": dim, "n": n, "ms": m, "s_per_point": m / 1e3 / n})
+            del pts, idx, d2
+            torch.cuda.empty_cache()
+    big = [o for o in out if o["dim"] == 3 and o["n"] == 10_000_000][0]
+    return {"workload": "n-sweep-uniform-k1", "metric": "time per point (build + k=1 graph) vs n",
+            "value": big["n"] / (big["ms"] / 1e3), "unit": "points/s (3D, n = 1e7)", "steps": args.steps,
+            "sweep": out}
 
 
 def bench_large_k(args):
