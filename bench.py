@@ -12,7 +12,7 @@ the timed region starts; L2 is flushed (256 MiB write) between steps.
 --impl reference times the CPU oracle (plain C, OpenMP over queries) on the
 host cores on a bounded sample of the same workload.  Other workloads:
 --workload 2d-uniform | dynamic | batched | differentiable | large-k | skewed |
-update-sweep | n-sweep.
+update-sweep | n-sweep | k-sweep.
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -423,7 +423,7 @@ def run_other(args, ws, rank, local):
     fn = {"2d-uniform": bench_2d, "dynamic": bench_dynamic, "batched": bench_batched,
           "differentiable": bench_differentiable, "large-k": bench_large_k,
           "skewed": bench_skewed, "update-sweep": bench_update_sweep,
-          "n-sweep": bench_n_sweep}.get(args.workload)
+          "n-sweep": bench_n_sweep, "k-sweep": bench_k_sweep}.get(args.workload)
     if fn is None:
         raise SystemExit("unknown workload %r" % args.workload)
     out = fn(args)
@@ -753,6 +753,34 @@ def bench_n_sweep(args):
     return {"workload": "n-sweep-uniform-k1", "metric": "time per point (build + k=1 graph) vs n",
             "value": big["n"] / (big["ms"] / 1e3), "unit": "points/s (3D, n = 1e7)", "steps": args.steps,
             "sweep": out}
+
+
+def bench_k_sweep(args):
+    """Time per neighbour against k (the paper's k sweep, Sec. 5): 3D uniform
+    10^7 points (the large-k workload's points), L = 16, one build, then the
+    all-points search for k = 1 .. 100 with the default mapping."""
+    import torch
+    from paper_2111_04182_gb300 import datagen, zd
+    w = datagen.workload_3d_uniform(n=args.n)
+    n = len(w["pts"])
+    t = zd.zd_build(torch.from_numpy(w["pts"]).cuda(), w["leaf_size"], w["coord_bits"])
+    out = []
+    for k in (1, 2, 5, 10, 15, 20, 25, 30, 40, 50, 60, 70, 80, 90, 100):
+        idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+        d2 = torch.empty((n, k), dtype=torch.int64, device="cuda")
+        ms = []
+        for rep in range(args.warmup + args.steps):
+            a, b = _events(2)
+            a.record(); t.knn(k, out=(idx, d2)); b.record(); b.synchronize()
+            if rep >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        m = float(np.median(ms))
+        out.append({"k": k, "ms": m, "s_per_neighbour": m / 1e3 / (n * k)})
+        del idx, d2
+    assert zd.zd_check() == 0
+    t.free()
+    return {"workload": "k-sweep-3d-uniform-%d" % n, "metric": "time per neighbour (all-points search) vs k",
+            "value": n / (out[3]["ms"] / 1e3), "unit": "queries/s (k = 10)", "steps": args.steps, "sweep": out}
 
 
 def bench_large_k(args):
