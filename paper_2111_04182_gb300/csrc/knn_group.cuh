@@ -431,6 +431,7 @@ int launch_knn_group_dim(const KnnArgs &a, cudaStream_t s)
     else if (a.k <= 8) launch_group_k<DIM, 8>(a, g, s, st);
     else if (a.k <= 10) launch_group_k<DIM, 10>(a, g, s, st);
     else if (a.k <= 16) launch_group_k<DIM, 16>(a, g, s, st);
+    else if (a.k <= 24) launch_group_k<DIM, 24>(a, g, s, st);
     else launch_group_k<DIM, 32>(a, g, s, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;

@@ -466,6 +466,7 @@ int launch_knn_dim(const KnnArgs &a, cudaStream_t s)
     else if (a.k <= 8) launch_knn_k<DIM, 8, FLOAT>(a, s, st);
     else if (a.k <= 10) launch_knn_k<DIM, 10, FLOAT>(a, s, st);
     else if (a.k <= 16) launch_knn_k<DIM, 16, FLOAT>(a, s, st);
+    else if (a.k <= 24) launch_knn_k<DIM, 24, FLOAT>(a, s, st);
     else launch_knn_k<DIM, 32, FLOAT>(a, s, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
