@@ -25,8 +25,8 @@
 // that beats the k-th best is inserted by the warp: its rank comes from one
 // ballot per register, and the slots from the rank up move up by one place
 // (a shuffle, lane 0 taking lane 31 of the register below), which drops the
-// old k-th best off the top.  For k > 64 (four registers) such single
-// insertions cost more than batching: candidates that beat the k-th best are
+// old k-th best off the top.  For k > 64 (three or four registers) such
+// single insertions cost more than batching: candidates that beat the k-th best are
 // appended to a per-warp pending block of 32 and merged when it holds
 // WIDE_FLUSH or more after a leaf, or would overflow -- the block is sorted
 // (bitonic), then, from the top register down, the larger half of (register,
@@ -121,7 +121,7 @@ struct WideQuery {
     int count; // entries appended while filling
     D *bufd;   // this warp's fill buffer [32 R]
     int *bufi;
-    D *pend_d; // this warp's pending block [32] (R >= 4)
+    D *pend_d; // this warp's pending block [32] (R >= 3)
     int *pend_i;
     int pc;     // pending candidates
     int *stk_n; // this warp's DFS stack [WIDE_STACK]
@@ -158,7 +158,26 @@ struct WideQuery {
             id[r] = j < 0 ? -1 : j < count ? bufi[j] : INT_MAX;
         }
         __syncwarp();
-        wide_sort<2, R>(d, id, lane);
+        if constexpr ((R & (R - 1)) == 0) {
+            wide_sort<2, R>(d, id, lane);
+        } else {
+            // not a power of two: sort a padded list (the padding is +inf and
+            // ends on top)
+            constexpr int RP = R < 4 ? 4 : 8;
+            D pd[RP];
+            int pi[RP];
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+                pd[r] = r < R ? d[r] : M::inf();
+                pi[r] = r < R ? id[r] : INT_MAX;
+            }
+            wide_sort<2, RP>(pd, pi, lane);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                d[r] = pd[r];
+                id[r] = pi[r];
+            }
+        }
         filling = false;
         refresh_kth();
     }
@@ -194,7 +213,7 @@ struct WideQuery {
         refresh_kth();
     }
 
-    // Merge the pending block into the list (R >= 4).
+    // Merge the pending block into the list (R >= 3).
     __device__ __forceinline__ void merge_pending()
     {
         __syncwarp();
@@ -265,7 +284,7 @@ struct WideQuery {
                 mask = __ballot_sync(WFULL, ok && rank >= placed);
                 if (count >= k || mask) finish_fill();
             }
-            if (R >= 4 && mask) {
+            if (R >= 3 && mask) {
                 bool acc = (mask >> lane) & 1;
                 int n = __popc(mask);
                 if (pc + n > 32) {
@@ -290,7 +309,7 @@ struct WideQuery {
                 if (wkey_lt(xd, xi, td, ti)) insert(xd, xi);
             }
         }
-        if (R >= 4 && pc >= WIDE_FLUSH) merge_pending();
+        if (R >= 3 && pc >= WIDE_FLUSH) merge_pending();
     }
 
     // searchDown (Algorithm 2) from node v whose box distance is dv.  Every
@@ -346,11 +365,11 @@ struct WideQuery {
 };
 
 template <int DIM, int R, bool FLOAT>
-__global__ void __launch_bounds__(32 * WIDE_WARPS, R >= 4 ? 6 : 8) k_knn_wide(KnnArgs a, u32 *status)
+__global__ void __launch_bounds__(32 * WIDE_WARPS, R >= 3 ? 6 : 8) k_knn_wide(KnnArgs a, u32 *status)
 {
     typedef Metric<FLOAT> M;
     typedef typename M::D D;
-    constexpr int PEND = R >= 4 ? 32 : 1;
+    constexpr int PEND = R >= 3 ? 32 : 1;
     __shared__ D s_bufd[WIDE_WARPS][32 * R];
     __shared__ int s_bufi[WIDE_WARPS][32 * R];
     __shared__ D s_pd[WIDE_WARPS][PEND];
@@ -439,7 +458,7 @@ __global__ void __launch_bounds__(32 * WIDE_WARPS, R >= 4 ? 6 : 8) k_knn_wide(Kn
             }
         }
         if (w.filling) w.finish_fill();
-        if (R >= 4 && w.pc > 0) w.merge_pending();
+        if (R >= 3 && w.pc > 0) w.merge_pending();
 
         const int k = a.k;
         int32_t *oi = a.out_idx + row * k;
@@ -470,6 +489,7 @@ int launch_knn_wide_dim(const KnnArgs &a, cudaStream_t s)
     u32 *st = status_word();
     const unsigned grid = grid_for(a.m, WIDE_WARPS, 152 * 64);
     if (a.k <= 64) k_knn_wide<DIM, 2, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
+    else if (a.k <= 96) k_knn_wide<DIM, 3, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
     else k_knn_wide<DIM, 4, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;

@@ -30,7 +30,7 @@ def _t(a):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("k,L", [(33, 16), (64, 16), (65, 4), (100, 16), (128, 33)])
+@pytest.mark.parametrize("k,L", [(33, 16), (64, 16), (65, 4), (80, 16), (96, 8), (97, 16), (100, 16), (128, 33)])
 def test_large_k_all_points(zd, oracle, dim, k, L):
     rng = np.random.default_rng(dim * 1000 + k)
     bits = 21 if dim == 3 else 20
@@ -57,7 +57,7 @@ def test_large_k_external_queries(zd, oracle, mode, dim):
     q = rng.integers(0, 2 ** 20, size=(5_003, dim)).astype(np.int32)
     q[:50] = pts[:50]
     t = zd.zd_build(_t(pts), 16, bits, shift=[3, 0, 17][:dim])
-    for k, mapping in ((100, 0), (47, 0x100), (47, 0x200)):
+    for k, mapping in ((100, 0), (90, 0), (47, 0x100), (47, 0x200)):
         idx, d2 = t.knn(k, queries=_t(q), mode=mode, mapping=mapping)
         assert zd.zd_check() == 0
         oi, od = oracle.knn_brute(pts, k, queries=q)
