@@ -820,7 +820,7 @@ def bench_large_k(args):
     return {"workload": "3d-uniform-1e7-k%d" % k, "metric": "queries/s (build + all-points k=%d)" % k,
             "value": n / ((bm + km) / 1e3), "unit": "queries/s", "build_ms": bm, "knn_ms": km,
             "knn_queries_per_s": n / (km / 1e3), "k": k, "steps": args.steps,
-            "roofline": {"kernel": "k_knn_wide<3,%d,0>" % (2 if k <= 64 else 4), "bound": "hbm",
+            "roofline": {"kernel": "k_knn_wide<3,%d,0>" % (2 if k <= 64 else 3 if k <= 96 else 4), "bound": "hbm",
                          "achieved": kb / (km / 1e3) / 1e9,
                          "peak": pk, "peak_source": pk_src, "unit": "GB/s",
                          "frac": kb / (km / 1e3) / 1e9 / pk, "traffic": traffic,
