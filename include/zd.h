@@ -82,9 +82,9 @@ enum { ZD_KNN_THREAD_PER_QUERY = 0x100, ZD_KNN_WARP_GROUP = 0x200 };
 enum { ZD_KNN_ALL_POINTS = 0x400 };
 
 /* Largest k of one search.  Up to 32 neighbours a query's list lives in one
- * thread's registers (both mappings above); for 32 < k <= ZD_MAX_K one warp
- * serves one query with the list spread over its lanes, whatever the mapping
- * flags say. */
+ * thread's registers (both mappings above), up to 40 under warp groups; for
+ * larger k (and for 32 < k <= 40 without warp groups) one warp serves one
+ * query with the list spread over its lanes. */
 #define ZD_MAX_K 128
 
 typedef struct zd_params {

@@ -577,7 +577,6 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
     // apart in a group, whose shared traversal then covers much more than
     // each query needs, and one thread per query is faster (measured: 10^6
     // queries into 5*10^7 points 2.9 vs 5.5 ms; 10^7 into 10^7 13.1 vs 11.1).
-    if (k > KNN_MAX_K_REG) return launch_knn_wide(a, s);
     // Warp groups serve leaf-based all points and bit-based external queries;
     // all points started from the root or by key bits run one thread per
     // query (Algorithms 2 / 3 as the paper states them).  By default groups
@@ -592,6 +591,8 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
     const bool group = (variant == ZD_KNN_WARP_GROUP || (variant == 0 && dense && k_ok)) &&
                        (allpts ? mode == ZD_SEARCH_LEAF
                                : ((mode == ZD_SEARCH_BIT && !t->cloud_off) || forest_ext));
+    // beyond the register lists: one warp per query
+    if (k > KNN_MAX_K_GROUP || (k > KNN_MAX_K_THREAD && !group)) return launch_knn_wide(a, s);
     if (!group) return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s);
     if (forest_ext) a.mode = ZD_SEARCH_BIT;
     Mem mem = mem_of(t, s);

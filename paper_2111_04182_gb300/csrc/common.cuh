@@ -182,7 +182,8 @@ int launch_group_starts(const int64_t *cloud_off, int64_t n_clouds, int64_t n_gr
                         int64_t *gpre, cudaStream_t s);
 
 // -------------------------------------------------------------------- knn
-constexpr int KNN_MAX_K_REG = 32; // largest k kept in one thread's registers
+constexpr int KNN_MAX_K_THREAD = 32; // largest k of the one-thread-per-query mapping
+constexpr int KNN_MAX_K_GROUP = 40;  // largest k of the warp-group mapping
 
 struct KnnArgs {
     TreeView t;
@@ -213,8 +214,8 @@ int launch_knn_i32(const KnnArgs &a, cudaStream_t s);
 int launch_knn_group_i32(const KnnArgs &a, cudaStream_t s); // + exact fallback
 int launch_knn_f32(const KnnArgs &a, cudaStream_t s);
 int launch_knn_group_f32(const KnnArgs &a, cudaStream_t s);
-// Large k (KNN_MAX_K_REG < k <= ZD_MAX_K): one warp per query, any mode and
-// mapping, integer or float.
+// Large k (above the thread / group limits, up to ZD_MAX_K): one warp per
+// query, any mode, integer or float.
 int launch_knn_wide(const KnnArgs &a, cudaStream_t s);
 
 // --------------------------------------------------------------- backward

@@ -432,7 +432,8 @@ int launch_knn_group_dim(const KnnArgs &a, cudaStream_t s)
     else if (a.k <= 10) launch_group_k<DIM, 10>(a, g, s, st);
     else if (a.k <= 16) launch_group_k<DIM, 16>(a, g, s, st);
     else if (a.k <= 24) launch_group_k<DIM, 24>(a, g, s, st);
-    else launch_group_k<DIM, 32>(a, g, s, st);
+    else if (a.k <= 32) launch_group_k<DIM, 32>(a, g, s, st);
+    else launch_group_k<DIM, 40>(a, g, s, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

@@ -322,7 +322,8 @@ int launch_knn_group_f_dim(const KnnArgs &a, cudaStream_t s)
     else if (a.k <= 10) k_knn_group_f<DIM, 10><<<g, KNN_THREADS, 0, s>>>(a, st);
     else if (a.k <= 16) k_knn_group_f<DIM, 16><<<g, KNN_THREADS, 0, s>>>(a, st);
     else if (a.k <= 24) k_knn_group_f<DIM, 24><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else k_knn_group_f<DIM, 32><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 32) k_knn_group_f<DIM, 32><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else k_knn_group_f<DIM, 40><<<g, KNN_THREADS, 0, s>>>(a, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

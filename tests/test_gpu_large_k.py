@@ -30,7 +30,7 @@ def _t(a):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("k,L", [(33, 16), (64, 16), (65, 4), (80, 16), (96, 8), (97, 16), (100, 16), (128, 33)])
+@pytest.mark.parametrize("k,L", [(33, 16), (40, 16), (41, 8), (64, 16), (65, 4), (80, 16), (96, 8), (97, 16), (100, 16), (128, 33)])
 def test_large_k_all_points(zd, oracle, dim, k, L):
     rng = np.random.default_rng(dim * 1000 + k)
     bits = 21 if dim == 3 else 20
@@ -40,11 +40,12 @@ def test_large_k_all_points(zd, oracle, dim, k, L):
     pts[:500] = pts[500:1000]  # duplicates: ties at d^2 = 0
     pts[1000:1200] = pts[1000]  # a leaf of equal keys, larger than L
     t = zd.zd_build(_t(pts), L, bits)
-    idx, d2 = t.knn(k)
-    assert zd.zd_check() == 0
     oi, od = oracle.OracleTree(pts, L, bits).knn(k)
-    assert np.array_equal(d2.cpu().numpy(), od)
-    assert np.array_equal(idx.cpu().numpy(), oi)
+    for mapping in (0, 0x100, 0x200):
+        idx, d2 = t.knn(k, mapping=mapping)
+        assert zd.zd_check() == 0
+        assert np.array_equal(d2.cpu().numpy(), od), mapping
+        assert np.array_equal(idx.cpu().numpy(), oi), mapping
     t.free()
 
 
@@ -57,7 +58,7 @@ def test_large_k_external_queries(zd, oracle, mode, dim):
     q = rng.integers(0, 2 ** 20, size=(5_003, dim)).astype(np.int32)
     q[:50] = pts[:50]
     t = zd.zd_build(_t(pts), 16, bits, shift=[3, 0, 17][:dim])
-    for k, mapping in ((100, 0), (90, 0), (47, 0x100), (47, 0x200)):
+    for k, mapping in ((100, 0), (90, 0), (47, 0x100), (47, 0x200), (38, 0x100), (38, 0x200)):
         idx, d2 = t.knn(k, queries=_t(q), mode=mode, mapping=mapping)
         assert zd.zd_check() == 0
         oi, od = oracle.knn_brute(pts, k, queries=q)
