@@ -786,7 +786,7 @@ def bench_k_sweep(args):
 def bench_large_k(args):
     """3D uniform, n = 10^7 in [0, 2^20)^3, L = 16, k = 100 (the paper's k
     sweep): build + all-points k-NN with ids and int64 d^2 written; for
-    32 < k one warp serves one query.  Outputs (12 GB) exceed L2.  Sampled
+    k > 40 one warp serves one query.  Outputs (12 GB) exceed L2.  Sampled
     rows are checked for properties any exact answer has."""
     import torch
     from paper_2111_04182_gb300 import datagen, zd
@@ -820,7 +820,8 @@ def bench_large_k(args):
     return {"workload": "3d-uniform-1e7-k%d" % k, "metric": "queries/s (build + all-points k=%d)" % k,
             "value": n / ((bm + km) / 1e3), "unit": "queries/s", "build_ms": bm, "knn_ms": km,
             "knn_queries_per_s": n / (km / 1e3), "k": k, "steps": args.steps,
-            "roofline": {"kernel": "k_knn_wide<3,%d,0>" % (2 if k <= 64 else 3 if k <= 96 else 4), "bound": "hbm",
+            "roofline": {"kernel": ("k_knn_group<3,40,fs>" if k <= 40 else
+                                    "k_knn_wide<3,%d,0>" % (2 if k <= 64 else 3 if k <= 96 else 4)), "bound": "hbm",
                          "achieved": kb / (km / 1e3) / 1e9,
                          "peak": pk, "peak_source": pk_src, "unit": "GB/s",
                          "frac": kb / (km / 1e3) / 1e9 / pk, "traffic": traffic,
