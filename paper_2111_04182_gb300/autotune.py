@@ -19,7 +19,7 @@ import torch
 
 from . import zd
 
-LEAF_SIZES = (8, 16, 32)
+LEAF_SIZES = (8, 16, 32, 64)
 MAPPINGS = {"thread": zd.ZD_KNN_THREAD_PER_QUERY, "warp_group": zd.ZD_KNN_WARP_GROUP}
 
 

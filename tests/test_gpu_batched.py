@@ -108,7 +108,7 @@ def test_batched_step_in_cuda_graph_matches_eager(zd, oracle):
     off_d = torch.from_numpy(off).to(DEV)
     n = int(off[-1])
     tune = autotune.tune_batched(pts, off, 16, 16, use_cache=False, reps=1)
-    assert tune["leaf_size"] in autotune.LEAF_SIZES and len(tune["table"]) == 6
+    assert tune["leaf_size"] in autotune.LEAF_SIZES and len(tune["table"]) == 2 * len(autotune.LEAF_SIZES)
     L, mp = tune["leaf_size"], tune["mapping"]
     idx = torch.full((n, 16), -7, dtype=torch.int32, device=DEV)
     d2 = torch.full((n, 16), -7, dtype=torch.int64, device=DEV)
