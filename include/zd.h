@@ -45,7 +45,8 @@ extern "C" {
 typedef enum zd_status {
     ZD_OK = 0,
     ZD_ERR_INVALID_ARG = 1,  /* bad argument (host-checked) */
-    ZD_ERR_RANGE = 2,        /* a shifted coordinate outside [0, 2^coord_bits) */
+    ZD_ERR_RANGE = 2,        /* a shifted integer coordinate outside [0, 2^coord_bits),
+                                or a float one non-finite or above 1e18 in magnitude */
     ZD_ERR_OOM = 3,          /* the allocator returned NULL */
     ZD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
     ZD_ERR_NOT_FOUND = 5,    /* delete of an id that is not live */
