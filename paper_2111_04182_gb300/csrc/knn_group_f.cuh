@@ -308,10 +308,11 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group_f(KnnArgs a, u32 *sta
     }
 }
 
+// Launchers split by list width so that the instantiations compile in
+// separate translation units (the wide lists are register-heavy).
 template <int DIM>
-int launch_knn_group_f_dim(const KnnArgs &a, cudaStream_t s)
+int launch_knn_group_f_narrow(const KnnArgs &a, cudaStream_t s) // k <= 16
 {
-    if (a.n_groups <= 0) return ZD_OK;
     const unsigned g = (unsigned)((a.n_groups * 32 + KNN_THREADS - 1) / KNN_THREADS);
     u32 *st = status_word();
     if (a.k <= 1) k_knn_group_f<DIM, 1><<<g, KNN_THREADS, 0, s>>>(a, st);
@@ -320,8 +321,17 @@ int launch_knn_group_f_dim(const KnnArgs &a, cudaStream_t s)
     else if (a.k <= 5) k_knn_group_f<DIM, 5><<<g, KNN_THREADS, 0, s>>>(a, st);
     else if (a.k <= 8) k_knn_group_f<DIM, 8><<<g, KNN_THREADS, 0, s>>>(a, st);
     else if (a.k <= 10) k_knn_group_f<DIM, 10><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else if (a.k <= 16) k_knn_group_f<DIM, 16><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else if (a.k <= 24) k_knn_group_f<DIM, 24><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else k_knn_group_f<DIM, 16><<<g, KNN_THREADS, 0, s>>>(a, st);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+template <int DIM>
+int launch_knn_group_f_wide(const KnnArgs &a, cudaStream_t s) // 16 < k <= 40
+{
+    const unsigned g = (unsigned)((a.n_groups * 32 + KNN_THREADS - 1) / KNN_THREADS);
+    u32 *st = status_word();
+    if (a.k <= 24) k_knn_group_f<DIM, 24><<<g, KNN_THREADS, 0, s>>>(a, st);
     else if (a.k <= 32) k_knn_group_f<DIM, 32><<<g, KNN_THREADS, 0, s>>>(a, st);
     else k_knn_group_f<DIM, 40><<<g, KNN_THREADS, 0, s>>>(a, st);
     ZD_CUDA(cudaGetLastError());
