@@ -430,8 +430,10 @@ int launch_knn_group_dim(const KnnArgs &a, cudaStream_t s)
     else if (a.k <= 5) launch_group_k<DIM, 5>(a, g, s, st);
     else if (a.k <= 8) launch_group_k<DIM, 8>(a, g, s, st);
     else if (a.k <= 10) launch_group_k<DIM, 10>(a, g, s, st);
+    else if (a.k <= 12) launch_group_k<DIM, 12>(a, g, s, st);
     else if (a.k <= 16) launch_group_k<DIM, 16>(a, g, s, st);
     else if (a.k <= 24) launch_group_k<DIM, 24>(a, g, s, st);
+    else if (a.k <= 28) launch_group_k<DIM, 28>(a, g, s, st);
     else if (a.k <= 32) launch_group_k<DIM, 32>(a, g, s, st);
     else launch_group_k<DIM, 40>(a, g, s, st);
     ZD_CUDA(cudaGetLastError());

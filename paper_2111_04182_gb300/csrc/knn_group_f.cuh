@@ -321,6 +321,7 @@ int launch_knn_group_f_narrow(const KnnArgs &a, cudaStream_t s) // k <= 16
     else if (a.k <= 5) k_knn_group_f<DIM, 5><<<g, KNN_THREADS, 0, s>>>(a, st);
     else if (a.k <= 8) k_knn_group_f<DIM, 8><<<g, KNN_THREADS, 0, s>>>(a, st);
     else if (a.k <= 10) k_knn_group_f<DIM, 10><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 12) k_knn_group_f<DIM, 12><<<g, KNN_THREADS, 0, s>>>(a, st);
     else k_knn_group_f<DIM, 16><<<g, KNN_THREADS, 0, s>>>(a, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
@@ -332,6 +333,7 @@ int launch_knn_group_f_wide(const KnnArgs &a, cudaStream_t s) // 16 < k <= 40
     const unsigned g = (unsigned)((a.n_groups * 32 + KNN_THREADS - 1) / KNN_THREADS);
     u32 *st = status_word();
     if (a.k <= 24) k_knn_group_f<DIM, 24><<<g, KNN_THREADS, 0, s>>>(a, st);
+    else if (a.k <= 28) k_knn_group_f<DIM, 28><<<g, KNN_THREADS, 0, s>>>(a, st);
     else if (a.k <= 32) k_knn_group_f<DIM, 32><<<g, KNN_THREADS, 0, s>>>(a, st);
     else k_knn_group_f<DIM, 40><<<g, KNN_THREADS, 0, s>>>(a, st);
     ZD_CUDA(cudaGetLastError());

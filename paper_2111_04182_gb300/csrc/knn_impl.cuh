@@ -465,8 +465,10 @@ int launch_knn_dim(const KnnArgs &a, cudaStream_t s)
     else if (a.k <= 5) launch_knn_k<DIM, 5, FLOAT>(a, s, st);
     else if (a.k <= 8) launch_knn_k<DIM, 8, FLOAT>(a, s, st);
     else if (a.k <= 10) launch_knn_k<DIM, 10, FLOAT>(a, s, st);
+    else if (a.k <= 12) launch_knn_k<DIM, 12, FLOAT>(a, s, st);
     else if (a.k <= 16) launch_knn_k<DIM, 16, FLOAT>(a, s, st);
     else if (a.k <= 24) launch_knn_k<DIM, 24, FLOAT>(a, s, st);
+    else if (a.k <= 28) launch_knn_k<DIM, 28, FLOAT>(a, s, st);
     else if (a.k <= 32) launch_knn_k<DIM, 32, FLOAT>(a, s, st);
     else launch_knn_k<DIM, 40, FLOAT>(a, s, st); // the exact fallback of 40-wide groups
     ZD_CUDA(cudaGetLastError());

@@ -130,7 +130,7 @@ MAPPINGS = [0x100, 0x200]  # one thread per query; one warp per 32-point group
 
 @pytest.mark.parametrize("mapping", MAPPINGS)
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("k", [1, 3, 5, 10, 16, 20, 24, 32])
+@pytest.mark.parametrize("k", [1, 3, 5, 10, 12, 16, 20, 24, 27, 32])
 def test_knn_all_points(zd, oracle, dim, k, mapping):
     rng = np.random.default_rng(dim * 1000 + k)
     bits = 21 if dim == 3 else 20
