@@ -282,41 +282,44 @@ __device__ __forceinline__ void search_down(const TreeView &t, int v, typename M
     int sn[KNN_STACK];
     D sd[KNN_STACK];
     int sp = 0;
-    sn[sp] = v;
-    sd[sp] = dv;
-    ++sp;
-    while (sp > 0) {
+    int u = v;
+    D du = dv;
+    while (true) {
+        if (du <= bd[K - 1]) { // else pruned by the (possibly shrunk) k-th distance
+            if (u < 0) {
+                scan_leaf<DIM, K, FLOAT>(t, ~u, self, q, pf, bd, bi);
+            } else {
+                const int2 ch = __ldg(t.ichild + u);
+                int4 al, ah, bl, bh;
+                node_box(t, ch.x, al, ah);
+                node_box(t, ch.y, bl, bh);
+                const D da = M::template boxd<DIM>(q, al, ah);
+                const D db = M::template boxd<DIM>(q, bl, bh);
+                const D thr = bd[K - 1];
+                // the farther child waits on the stack; the nearer one is
+                // searched next without a round trip through the stack
+                const int nf = da <= db ? ch.y : ch.x, nn = da <= db ? ch.x : ch.y;
+                const D df = da <= db ? db : da, dn = da <= db ? da : db;
+                if (df <= thr) {
+                    if (sp + 1 > KNN_STACK) {
+                        set_status(status, ZD_ERR_CUDA);
+                        return;
+                    }
+                    sn[sp] = nf;
+                    sd[sp] = df;
+                    ++sp;
+                }
+                if (dn <= thr) {
+                    u = nn;
+                    du = dn;
+                    continue;
+                }
+            }
+        }
+        if (sp == 0) break;
         --sp;
-        const int u = sn[sp];
-        if (sd[sp] > bd[K - 1]) continue; // pruned by the (possibly shrunk) k-th distance
-        if (u < 0) {
-            scan_leaf<DIM, K, FLOAT>(t, ~u, self, q, pf, bd, bi);
-            continue;
-        }
-        const int2 ch = __ldg(t.ichild + u);
-        int4 al, ah, bl, bh;
-        node_box(t, ch.x, al, ah);
-        node_box(t, ch.y, bl, bh);
-        const D da = M::template boxd<DIM>(q, al, ah);
-        const D db = M::template boxd<DIM>(q, bl, bh);
-        const D thr = bd[K - 1];
-        // push the farther child first so the nearer one is searched first
-        const int nf = da <= db ? ch.y : ch.x, nn = da <= db ? ch.x : ch.y;
-        const D df = da <= db ? db : da, dn = da <= db ? da : db;
-        if (sp + 2 > KNN_STACK) {
-            set_status(status, ZD_ERR_CUDA);
-            return;
-        }
-        if (df <= thr) {
-            sn[sp] = nf;
-            sd[sp] = df;
-            ++sp;
-        }
-        if (dn <= thr) {
-            sn[sp] = nn;
-            sd[sp] = dn;
-            ++sp;
-        }
+        u = sn[sp];
+        du = sd[sp];
     }
 }
 

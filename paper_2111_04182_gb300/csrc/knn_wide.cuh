@@ -312,53 +312,60 @@ struct WideQuery {
         if (R >= 3 && pc >= WIDE_FLUSH) merge_pending();
     }
 
-    // searchDown (Algorithm 2) from node v whose box distance is dv.  Every
-    // lane pushes and pops the same entries; the __syncwarp after a pop keeps
-    // a lane from overwriting the entry before all lanes have read it.
+    // searchDown (Algorithm 2) from node v whose box distance is dv.  The
+    // nearer child is searched next directly; the farther one waits on the
+    // stack, which every lane pushes and pops identically -- the __syncwarp
+    // after a pop keeps a lane from overwriting the entry before all lanes
+    // have read it.
     __device__ __forceinline__ bool search_down(int v, D dv, u32 *status)
     {
-        stk_n[0] = v;
-        stk_d[0] = dv;
-        int sp = 1;
-        while (sp > 0) {
-            --sp;
-            const int u = stk_n[sp];
-            const D du = stk_d[sp];
-            __syncwarp();
-            if (du > td) continue; // pruned by the (possibly shrunk) k-th distance
-            if (u < 0) {
-                scan_leaf(~u);
-                continue;
-            }
-            if (R == 2) {
-                const int2 rg = __ldg(t.irange + u);
-                if (rg.y - rg.x <= WIDE_SMALL_SUBTREE) {
-                    scan_range(rg.x, rg.y);
-                    continue;
+        int sp = 0;
+        int u = v;
+        D du = dv;
+        while (true) {
+            if (du <= td) { // else pruned by the (possibly shrunk) k-th distance
+                if (u < 0) {
+                    scan_leaf(~u);
+                } else {
+                    bool expand = true;
+                    if (R == 2) {
+                        const int2 rg = __ldg(t.irange + u);
+                        if (rg.y - rg.x <= WIDE_SMALL_SUBTREE) {
+                            scan_range(rg.x, rg.y);
+                            expand = false;
+                        }
+                    }
+                    if (expand) {
+                        const int2 ch = __ldg(t.ichild + u);
+                        int4 al, ah, bl, bh;
+                        node_box(t, ch.x, al, ah);
+                        node_box(t, ch.y, bl, bh);
+                        const D da = M::template boxd<DIM>(q, al, ah);
+                        const D db = M::template boxd<DIM>(q, bl, bh);
+                        const int nf = da <= db ? ch.y : ch.x, nn = da <= db ? ch.x : ch.y;
+                        const D df = da <= db ? db : da, dn = da <= db ? da : db;
+                        if (df <= td) {
+                            if (sp + 1 > WIDE_STACK) {
+                                if (lane == 0) set_status(status, ZD_ERR_CUDA);
+                                return false;
+                            }
+                            stk_n[sp] = nf;
+                            stk_d[sp] = df;
+                            ++sp;
+                        }
+                        if (dn <= td) {
+                            u = nn;
+                            du = dn;
+                            continue;
+                        }
+                    }
                 }
             }
-            const int2 ch = __ldg(t.ichild + u);
-            int4 al, ah, bl, bh;
-            node_box(t, ch.x, al, ah);
-            node_box(t, ch.y, bl, bh);
-            const D da = M::template boxd<DIM>(q, al, ah);
-            const D db = M::template boxd<DIM>(q, bl, bh);
-            const int nf = da <= db ? ch.y : ch.x, nn = da <= db ? ch.x : ch.y;
-            const D df = da <= db ? db : da, dn = da <= db ? da : db;
-            if (sp + 2 > WIDE_STACK) {
-                if (lane == 0) set_status(status, ZD_ERR_CUDA);
-                return false;
-            }
-            if (df <= td) {
-                stk_n[sp] = nf;
-                stk_d[sp] = df;
-                ++sp;
-            }
-            if (dn <= td) {
-                stk_n[sp] = nn;
-                stk_d[sp] = dn;
-                ++sp;
-            }
+            if (sp == 0) break;
+            --sp;
+            u = stk_n[sp];
+            du = stk_d[sp];
+            __syncwarp();
         }
         return true;
     }
