@@ -1,0 +1,55 @@
+"""Host-side pieces of bench.py and the committed profile summaries (no GPU)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_headline_config_keys(bench):
+    c = bench.headline_config(10_000_000, 10, 16, 21, "1 GPU")
+    assert c["workload"] == "3d-clustered-1e7"
+    for key in ("n", "dim", "k", "leaf_size", "coord_bits", "l2", "parallelism"):
+        assert key in c
+
+
+def test_algorithmic_bytes(bench):
+    assert bench.knn_bytes_per_query(10) == 148
+    assert bench.knn_bytes_per_query(100) == 1228
+    assert 250 <= bench.build_bytes_per_point() <= 300
+
+
+def test_profiled_traffic_follows_the_sources(bench, tmp_path, monkeypatch):
+    """A traffic line counts only while its source digest matches."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    src = tmp_path / "k.cuh"
+    src.write_text("kernel v1")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    dig = bench.source_digest(["k.cuh"])
+    (prof / "p.md").write_text("traffic_bytes_per_launch: 123 source: %s kernel: kk workload: ww\n" % dig)
+    assert bench.profiled_traffic("kk", "ww", "p.md", ["k.cuh"]) == 123
+    assert bench.profiled_traffic("kk", "other", "p.md", ["k.cuh"]) is None
+    src.write_text("kernel v2")
+    assert bench.profiled_traffic("kk", "ww", "p.md", ["k.cuh"]) is None
+
+
+def test_profile_commands_run_committed_files():
+    """Every command quoted in profiles/ runs a committed file, never a
+    scratch one."""
+    pdir = os.path.join(ROOT, "profiles")
+    for f in os.listdir(pdir):
+        text = open(os.path.join(pdir, f)).read()
+        assert "_work" not in text, f
+        for m in re.finditer(r"python (\S+\.py)", text):
+            assert os.path.exists(os.path.join(ROOT, m.group(1))), (f, m.group(1))
