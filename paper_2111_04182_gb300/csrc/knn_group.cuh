@@ -218,46 +218,49 @@ __device__ __forceinline__ void group_search(const TreeView &t, int start, int l
                                              float &thr_f, u32 *status)
 {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) stack[0] = start;
-    int sp = 1;
-    __syncwarp();
-    while (sp > 0) {
-        const int v = stack[--sp];
-        __syncwarp();
-        if (v < 0 && ~v >= l0 && ~v <= l1) continue; // scanned already
-        bool need;
-        float4 flo, fhi;
-        if (FS) {
-            const float4 *fb = v < 0 ? t.flbox + 2 * (~v) : t.fibox + 2 * v;
-            flo = __ldg(fb);
-            fhi = __ldg(fb + 1);
-            need = c.live && box_d2f<DIM>(c, flo, fhi) <= thr_f;
-        } else {
-            int4 lo, hi;
-            node_box(t, v, lo, hi);
-            need = c.live && box_d2<DIM>(c, lo, hi) <= thr;
-        }
-        if (!__any_sync(0xffffffffu, need)) continue;
-        if (v < 0) {
+    int sp = 0;
+    int v = start;
+    while (true) {
+        // the nearer child is searched next directly; the farther one waits
+        // on the stack (lane 0 writes it, every lane holds the same pointer)
+        if (!(v < 0 && ~v >= l0 && ~v <= l1)) { // else scanned already
+            bool need;
+            float4 flo, fhi;
             if (FS) {
-                group_scan_f<DIM, K>(t, __float_as_int(flo.w), __float_as_int(fhi.w), c, key, thr, thr_f);
+                const float4 *fb = v < 0 ? t.flbox + 2 * (~v) : t.fibox + 2 * v;
+                flo = __ldg(fb);
+                fhi = __ldg(fb + 1);
+                need = c.live && box_d2f<DIM>(c, flo, fhi) <= thr_f;
             } else {
-                const int a = __ldg(t.leaf_lo + ~v), b = __ldg(t.leaf_lo + ~v + 1);
-                group_scan<DIM, K>(t, a, b, c, key, thr);
+                int4 lo, hi;
+                node_box(t, v, lo, hi);
+                need = c.live && box_d2<DIM>(c, lo, hi) <= thr;
             }
-            continue;
+            if (__any_sync(0xffffffffu, need)) {
+                if (v < 0) {
+                    if (FS) {
+                        group_scan_f<DIM, K>(t, __float_as_int(flo.w), __float_as_int(fhi.w), c, key, thr, thr_f);
+                    } else {
+                        const int a = __ldg(t.leaf_lo + ~v), b = __ldg(t.leaf_lo + ~v + 1);
+                        group_scan<DIM, K>(t, a, b, c, key, thr);
+                    }
+                } else {
+                    const int2 ch = FS ? make_int2(__float_as_int(flo.w), __float_as_int(fhi.w)) : __ldg(t.ichild + v);
+                    const bool right_first = (mid_key >> __ldg(t.ibit + v)) & 1;
+                    if (sp + 1 > GROUP_STACK) {
+                        if (lane == 0) set_status(status, ZD_ERR_CUDA);
+                        return;
+                    }
+                    if (lane == 0) stack[sp] = right_first ? ch.x : ch.y; // the far child waits
+                    ++sp;
+                    __syncwarp();
+                    v = right_first ? ch.y : ch.x;
+                    continue;
+                }
+            }
         }
-        const int2 ch = FS ? make_int2(__float_as_int(flo.w), __float_as_int(fhi.w)) : __ldg(t.ichild + v);
-        const bool right_first = (mid_key >> __ldg(t.ibit + v)) & 1;
-        if (sp + 2 > GROUP_STACK) {
-            if (lane == 0) set_status(status, ZD_ERR_CUDA);
-            return;
-        }
-        if (lane == 0) {
-            stack[sp] = right_first ? ch.x : ch.y; // the far child waits below
-            stack[sp + 1] = right_first ? ch.y : ch.x;
-        }
-        sp += 2;
+        if (sp == 0) break;
+        v = stack[--sp];
         __syncwarp();
     }
 }

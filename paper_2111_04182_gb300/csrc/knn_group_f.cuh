@@ -145,31 +145,34 @@ __device__ __forceinline__ void group_search_ff(const TreeView &t, int start, in
                                                 int *stack, const GroupCtxF &c, EstList<K> &L, u32 *status)
 {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) stack[0] = start;
-    int sp = 1;
-    __syncwarp();
-    while (sp > 0) {
-        const int v = stack[--sp];
-        __syncwarp();
-        if (v < 0 && ~v >= l0 && ~v <= l1) continue; // scanned already
-        const float4 *b = (const float4 *)(v < 0 ? t.lbox + 2 * (~v) : t.ibox + 2 * v);
-        const bool need = c.live && box_est<DIM>(c, __ldg(b), __ldg(b + 1)) <= L.thr;
-        if (!__any_sync(0xffffffffu, need)) continue;
-        if (v < 0) {
-            group_scan_ff<DIM, K>(t, __ldg(t.leaf_lo + ~v), __ldg(t.leaf_lo + ~v + 1), c, L);
-            continue;
+    int sp = 0;
+    int v = start;
+    while (true) {
+        // the nearer child is searched next directly; the farther one waits
+        // on the stack (lane 0 writes it, every lane holds the same pointer)
+        if (!(v < 0 && ~v >= l0 && ~v <= l1)) { // else scanned already
+            const float4 *b = (const float4 *)(v < 0 ? t.lbox + 2 * (~v) : t.ibox + 2 * v);
+            const bool need = c.live && box_est<DIM>(c, __ldg(b), __ldg(b + 1)) <= L.thr;
+            if (__any_sync(0xffffffffu, need)) {
+                if (v < 0) {
+                    group_scan_ff<DIM, K>(t, __ldg(t.leaf_lo + ~v), __ldg(t.leaf_lo + ~v + 1), c, L);
+                } else {
+                    const int2 ch = __ldg(t.ichild + v);
+                    const bool right_first = (mid_key >> __ldg(t.ibit + v)) & 1;
+                    if (sp + 1 > GROUP_STACK) {
+                        if (lane == 0) set_status(status, ZD_ERR_CUDA);
+                        return;
+                    }
+                    if (lane == 0) stack[sp] = right_first ? ch.x : ch.y; // the far child waits
+                    ++sp;
+                    __syncwarp();
+                    v = right_first ? ch.y : ch.x;
+                    continue;
+                }
+            }
         }
-        const int2 ch = __ldg(t.ichild + v);
-        const bool right_first = (mid_key >> __ldg(t.ibit + v)) & 1;
-        if (sp + 2 > GROUP_STACK) {
-            if (lane == 0) set_status(status, ZD_ERR_CUDA);
-            return;
-        }
-        if (lane == 0) {
-            stack[sp] = right_first ? ch.x : ch.y;
-            stack[sp + 1] = right_first ? ch.y : ch.x;
-        }
-        sp += 2;
+        if (sp == 0) break;
+        v = stack[--sp];
         __syncwarp();
     }
 }
