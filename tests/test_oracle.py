@@ -217,6 +217,28 @@ def test_knn_external_queries_bit_and_root(oracle, mode):
         assert np.array_equal(idx, bi) and np.array_equal(d2, bd)
 
 
+@pytest.mark.parametrize("name", ["2DinCube", "2Dkuzmin", "3DonSphere", "3DinCube", "3Dplummer"])
+def test_knn_skewed_sets_vs_numpy_brute(oracle, name):
+    """The five point sets of the search-start comparison, small: the
+    oracle's tree search (all points, and external queries from both starts)
+    equals numpy brute force, at k = 1 and 12."""
+    from paper_2111_04182_gb300 import datagen
+    w = datagen.workload_skewed(name, n=2500)
+    pts, bits = w["pts"], w["coord_bits"]
+    t = oracle.OracleTree(pts, 16, bits)
+    rng = np.random.default_rng(9)
+    q = pts[rng.choice(len(pts), 200, replace=False)] + rng.integers(-3, 4, size=(200, w["dim"])).astype(np.int32)
+    q = np.clip(q, 0, 2 ** (bits - (1 if w["dim"] == 3 else 0)) - 1).astype(np.int32)
+    for k in (1, 12):
+        idx, d2 = t.knn(k)
+        bi, bd = brute_knn(pts, k)
+        assert np.array_equal(idx, bi) and np.array_equal(d2, bd), k
+        for mode in (1, 2):
+            idx, d2 = t.knn(k, queries=q, mode=mode)
+            bi, bd = brute_knn(pts, k, queries=q)
+            assert np.array_equal(idx, bi) and np.array_equal(d2, bd), (k, mode)
+
+
 def test_knn_lattice_closed_form(oracle):
     # Interior points of the unit lattice have exactly 2d neighbours at d^2 = 1.
     for dim in (2, 3):
