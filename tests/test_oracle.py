@@ -253,6 +253,33 @@ def test_knn_lattice_closed_form(oracle):
                 assert idx[i, : 2 * dim].tolist() == sorted(nb.tolist())
 
 
+def _floats(rows):
+    return np.array([[float(v) for v in r] for r in rows], np.float32)
+
+
+@pytest.mark.parametrize("case", GOLD["quantize"]["frames"], ids=lambda c: c["name"])
+def test_quantize_frame_hand_values(oracle, case):
+    # Sec. 3.1 "Numerical details": the frame (per-axis minimum, one common
+    # scale from the largest extent), the floored grid and the Morton keys
+    # of the tree built on it, all worked out by hand.
+    pts = _floats(case["pts"])
+    lo, scale = oracle.quantization_of(pts, case["bits"])
+    assert lo.tolist() == case["lo"] and scale == case["scale"]
+    q = oracle.quantize(pts, lo, scale, case["bits"])
+    assert q.tolist() == case["q"]
+    t = oracle.OracleTree(pts, 1, case["bits"], qlo=lo, qscale=scale)
+    e = t.export()
+    assert sorted(int(k) for k in e["keys"]) == sorted(int(k) for k in case["keys"])
+    assert [int(e["keys"][i]) for i in np.argsort(e["ids"])] == [int(k) for k in case["keys"]]
+
+
+@pytest.mark.parametrize("case", GOLD["quantize"]["explicit"], ids=lambda c: c["name"])
+def test_quantize_explicit_hand_values(oracle, case):
+    # Floor, clamp to [0, 2^B - 1], NaN -> 0, and the product taken in fp64.
+    q = oracle.quantize(_floats(case["pts"]), np.array(case["lo"]), case["scale"], case["bits"])
+    assert q.tolist() == case["q"]
+
+
 def test_knn_float_fp64_ranking(oracle):
     rng = np.random.default_rng(8)
     a = rng.standard_normal((400, 3)).astype(np.float32)

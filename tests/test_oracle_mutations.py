@@ -41,19 +41,29 @@ MUTATIONS = {
                                    "if (x->id != y->id) return x->id < y->id ? 1 : -1;"),
     "wrong child searched while climbing": ("search_down(t, P->left == c ? P->right : P->left, q, N);",
                                             "search_down(t, P->left == c ? P->left : P->right, q, N);"),
+    "quantize rounds instead of flooring": ("double v = floor(((double)pts[i * dim + j] - lo[j]) * scale);",
+                                            "double v = round(((double)pts[i * dim + j] - lo[j]) * scale);"),
+    "quantize in fp32": ("double v = floor(((double)pts[i * dim + j] - lo[j]) * scale);",
+                         "double v = floor((float)((float)pts[i * dim + j] - (float)lo[j]) * (float)scale);"),
+    "quantize clamps at 2^B": ("const double top = (double)(((int64_t)1 << coord_bits) - 1);",
+                               "const double top = (double)((int64_t)1 << coord_bits);"),
+    # the frame lives in the Python half of the oracle
+    "per-axis scale (last axis's extent)": ("oracle.py", "ext = float(np.max(hi - lo))", "ext = float((hi - lo)[-1])"),
+    "one minimum for all axes": ("oracle.py", "lo = pts.min(axis=0).astype(np.float64)",
+                                 "lo = np.full(pts.shape[1], pts.min(), np.float64)"),
 }
 
 
 def _load_variant(tmp, name, mutate=None):
     d = os.path.join(tmp, name.replace(" ", "_"))
     os.makedirs(d)
-    src = open(os.path.join(ROOT, "oracle", "zd_oracle.c")).read()
+    files = {f: open(os.path.join(ROOT, "oracle", f)).read() for f in ("zd_oracle.c", "oracle.py")}
     if mutate:
-        old, new = mutate
-        assert src.count(old) >= 1, "mutation anchor not found: %r" % old[:60]
-        src = src.replace(old, new, 1)
-    open(os.path.join(d, "zd_oracle.c"), "w").write(src)
-    shutil.copy(os.path.join(ROOT, "oracle", "oracle.py"), os.path.join(d, "oracle.py"))
+        target, old, new = mutate if len(mutate) == 3 else ("zd_oracle.c",) + tuple(mutate)
+        assert files[target].count(old) >= 1, "mutation anchor not found: %r" % old[:60]
+        files[target] = files[target].replace(old, new, 1)
+    for f, src in files.items():
+        open(os.path.join(d, f), "w").write(src)
     spec = importlib.util.spec_from_file_location("oracle_" + os.path.basename(d), os.path.join(d, "oracle.py"))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
@@ -61,9 +71,29 @@ def _load_variant(tmp, name, mutate=None):
     return mod
 
 
+def _quantize_pins(o) -> bool:
+    for case in GOLD["quantize"]["frames"]:
+        pts = np.array(case["pts"], np.float32)
+        lo, scale = o.quantization_of(pts, case["bits"])
+        if lo.tolist() != case["lo"] or scale != case["scale"]:
+            return False
+        if o.quantize(pts, lo, scale, case["bits"]).tolist() != case["q"]:
+            return False
+        e = o.OracleTree(pts, 1, case["bits"], qlo=lo, qscale=scale).export()
+        if [int(e["keys"][i]) for i in np.argsort(e["ids"])] != [int(k) for k in case["keys"]]:
+            return False
+    for case in GOLD["quantize"]["explicit"]:
+        pts = np.array([[float(v) for v in r] for r in case["pts"]], np.float32)
+        if o.quantize(pts, np.array(case["lo"]), case["scale"], case["bits"]).tolist() != case["q"]:
+            return False
+    return True
+
+
 def _pins(o) -> bool:
     """A quick subset of the pins; True iff all hold."""
     try:
+        if not _quantize_pins(o):
+            return False
         for case in GOLD["morton"]["cases"]:
             if max(case["pt"]) >= 2 ** 31:
                 continue
