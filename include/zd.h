@@ -53,7 +53,9 @@ typedef enum zd_status {
     ZD_ERR_DUPLICATE_ID = 6, /* the same id twice in one delete batch */
     ZD_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
     ZD_ERR_UNIMPLEMENTED = 8,/* a parameter combination not built (e.g. k > ZD_MAX_K) */
-    ZD_ERR_CAPACITY = 9      /* an insert beyond the tree's capacity */
+    ZD_ERR_CAPACITY = 9      /* beyond a size limit: an insert past the tree's
+                                capacity, or more than ZD_MAX_KEYS keys (or
+                                ZD_NOALLOC_MAX_KEYS for the no-allocation sort) */
 } zd_status;
 
 enum { ZD_COORD_I32 = 0, ZD_COORD_F32 = 1 };
@@ -87,6 +89,14 @@ enum { ZD_KNN_ALL_POINTS = 0x400 };
  * larger k (and for 32 < k <= 40 without warp groups) one warp serves one
  * query with the list spread over its lanes. */
 #define ZD_MAX_K 128
+
+/* Most keys one radix sort handles: the points of a tree (its capacity
+ * included) or of a forest, the external queries of one zd_knn /
+ * zd_knn_batched call, the keys of one zd_morton_sort and the (query,
+ * neighbour) pairs of one zd_knn_dist_backward.  The sort's look-back words
+ * carry a digit's running count in 30 bits.  Larger sizes return
+ * ZD_ERR_CAPACITY before any work is enqueued. */
+#define ZD_MAX_KEYS 1073741823 /* 2^30 - 1 */
 
 typedef struct zd_params {
     int32_t dim;        /* 2 or 3 */
@@ -151,7 +161,8 @@ int zd_morton_encode(const zd_params *p, const int32_t *d_pts, int64_t n, uint64
  * d_keys_out [n] gets the keys ascending and d_perm_out [n] the input
  * position of each output (equal keys keep input order).  key_bits (1..64)
  * bounds the significant low bits; digits above it are not sorted.  Scratch
- * comes from `alloc` (NULL: cudaMallocAsync). */
+ * comes from `alloc` (NULL: cudaMallocAsync).  n > ZD_MAX_KEYS returns
+ * ZD_ERR_CAPACITY. */
 int zd_morton_sort(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t *d_keys_out,
                    int32_t *d_perm_out, const zd_allocator *alloc, void *stream);
 
@@ -184,7 +195,8 @@ int zd_morton_sort_noalloc(const uint64_t *d_keys_in, int64_t n, int key_bits, u
  * float queries).  Integer coordinates outside the shifted universe record
  * ZD_ERR_RANGE too.  The point data is copied; the
  * caller may free d_pts after the call's work is done.  *out receives the
- * handle (free with zd_free). */
+ * handle (free with zd_free).  n or capacity above ZD_MAX_KEYS returns
+ * ZD_ERR_CAPACITY. */
 int zd_build(const zd_params *p, const zd_allocator *alloc, const void *d_pts, int64_t n,
              void *stream, zd_tree **out);
 

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libzd (declared in include/zd.h): argument checks,
 // tree lifetime and memory, and the sequencing of the kernels of each step.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -15,15 +16,19 @@ static __device__ u32 g_status;
 namespace zdk {
 u32 *status_word()
 {
-    static u32 *addr[64] = {nullptr};
+    // per-device cache of the symbol's device address; atomic entries, so two
+    // host threads making their first call at once store the same value
+    static std::atomic<u32 *> addr[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!addr[dev]) {
+    u32 *a = addr[dev].load(std::memory_order_acquire);
+    if (!a) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-        addr[dev] = (u32 *)p;
+        a = (u32 *)p;
+        addr[dev].store(a, std::memory_order_release);
     }
-    return addr[dev];
+    return a;
 }
 
 void *Mem::get(size_t bytes)
@@ -318,6 +323,7 @@ int zd_morton_sort(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t 
 {
     if (n < 0 || key_bits < 1 || key_bits > 64) return ZD_ERR_INVALID_ARG;
     if (n > 0 && (!d_keys_in || !d_keys_out || !d_perm_out)) return ZD_ERR_INVALID_ARG;
+    if (n > ZD_MAX_KEYS) return ZD_ERR_CAPACITY;
     if (!status_word()) return ZD_ERR_CUDA;
     Mem m;
     m.a = alloc;
@@ -333,8 +339,9 @@ int zd_build(const zd_params *p, const zd_allocator *alloc, const void *d_pts, i
     if (!out) return ZD_ERR_INVALID_ARG;
     *out = nullptr;
     ZD_TRY(check_params(p));
-    if (n < 0 || n >= ((int64_t)1 << 31) - 2 || (n > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
     if (p->capacity > 0 && p->capacity < n) return ZD_ERR_INVALID_ARG;
+    if (n > ZD_MAX_KEYS || p->capacity > ZD_MAX_KEYS) return ZD_ERR_CAPACITY;
     if (!status_word()) return ZD_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     zd_tree *t = tree_new(p, alloc);
@@ -384,7 +391,8 @@ int zd_build_batched(const zd_params *p, const zd_allocator *alloc, const void *
         max_seg = std::max(max_seg, sz);
     }
     const int64_t n = h_offsets[n_clouds];
-    if (n >= ((int64_t)1 << 31) - 2 || (n > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
+    if (n > 0 && !d_pts) return ZD_ERR_INVALID_ARG;
+    if (n > ZD_MAX_KEYS) return ZD_ERR_CAPACITY;
     const int cbits = ceil_log2(n_clouds);
     const int B = std::min(p->coord_bits, (64 - cbits) / p->dim);
     if (B < 1) return ZD_ERR_INVALID_ARG;
@@ -638,7 +646,8 @@ extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k,
         return run_knn(t, nullptr, nullptr, t->n, k, base | flags, d_idx, d_dist, s);
     }
     mode = base;
-    if (m < 0 || m >= ((int64_t)1 << 31) - 2 || (m > 0 && !d_queries)) return ZD_ERR_INVALID_ARG;
+    if (m < 0 || (m > 0 && !d_queries)) return ZD_ERR_INVALID_ARG;
+    if (m > ZD_MAX_KEYS) return ZD_ERR_CAPACITY;
     if (m == 0) return ZD_OK;
     Mem mem = mem_of(t, s);
     Scratch<u64> qkeys(mem, m);
@@ -659,7 +668,8 @@ extern "C" int zd_knn_batched(const zd_tree *t, const void *d_queries, const int
     cudaStream_t s = (cudaStream_t)stream;
     if (!d_queries)
         return run_knn(t, nullptr, nullptr, t->n, k, ZD_SEARCH_LEAF | mode_flags, d_idx, d_dist, s);
-    if (!d_query_offsets || m < 0 || m >= ((int64_t)1 << 31) - 2) return ZD_ERR_INVALID_ARG;
+    if (!d_query_offsets || m < 0) return ZD_ERR_INVALID_ARG;
+    if (m > ZD_MAX_KEYS) return ZD_ERR_CAPACITY;
     if (m == 0) return ZD_OK;
     Mem mem = mem_of(t, s);
     Scratch<u64> qkeys(mem, m);
@@ -762,8 +772,10 @@ extern "C" int zd_knn_dist_backward(const float *d_q, const float *d_ref, const 
                                     float *d_gref, void *stream)
 {
     if (batch < 0 || m < 0 || r < 0 || k < 1 || (dim != 2 && dim != 3)) return ZD_ERR_INVALID_ARG;
-    if (batch * m * k >= ((int64_t)1 << 31) - 2 || batch * r >= ((int64_t)1 << 31) - 2)
-        return ZD_ERR_INVALID_ARG;
+    // (each factor is bounded first so that the products cannot overflow)
+    if (batch > ZD_MAX_KEYS || m > ZD_MAX_KEYS || r > ZD_MAX_KEYS || k > ZD_MAX_K ||
+        batch * m > ZD_MAX_KEYS || batch * m * k > ZD_MAX_KEYS || batch * r > ZD_MAX_KEYS)
+        return ZD_ERR_CAPACITY;
     if (!d_gout || (batch * m > 0 && (!d_q || !d_idx || !d_gq)) || (batch * r > 0 && (!d_ref || !d_gref)))
         return ZD_ERR_INVALID_ARG;
     if (!status_word()) return ZD_ERR_CUDA;

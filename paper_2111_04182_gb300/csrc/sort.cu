@@ -8,6 +8,8 @@
 // look-back over the tiles before it, so a pass reads and writes the keys
 // exactly once.  Passes whose digit is the same for every key are skipped on
 // the device (no host round trip).  Every look-back wait is bounded.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace zdk {
@@ -292,7 +294,9 @@ constexpr int SORT_THREADS = 256; // one thread per digit in the look-back
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-// look-back word: 2 flag bits + 30-bit count (a tile holds < 2^30 keys)
+// look-back word: 2 flag bits + a 30-bit count.  The count is a digit's
+// running total over all tiles up to this one, so it is bounded by n, and n
+// is at most ZD_MAX_KEYS = 2^30 - 1 (checked in radix_sort).
 constexpr u32 LB_AGG = 1u << 30;
 constexpr u32 LB_INC = 2u << 30;
 constexpr u32 LB_COUNT = (1u << 30) - 1;
@@ -497,7 +501,8 @@ int radix_sort(const u64 *keys_in, int64_t n, int key_bits, u64 *keys_out, int32
                u32 *hist, Mem &mem)
 {
     if (n < 0 || key_bits < 1 || key_bits > 64) return ZD_ERR_INVALID_ARG;
-    if (n > (int64_t)0x7fffffff) return ZD_ERR_INVALID_ARG;
+    static_assert(ZD_MAX_KEYS <= LB_COUNT, "look-back counts must hold n");
+    if (n > ZD_MAX_KEYS) return ZD_ERR_CAPACITY;
     if (n == 0) return ZD_OK;
     cudaStream_t s = mem.s;
     const int npasses = (key_bits + RADIX_BITS - 1) / RADIX_BITS;
@@ -575,18 +580,21 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 // Device address of the scratch array on the current device.  In host code
 // the symbol itself is only a host-side stand-in, so the address is looked
 // up once per device (cudaGetSymbolAddress, with that device current) and
-// cached.
+// cached.  The cache entries are atomics: two host threads making their first
+// call at once both look the address up and store the same value.
 static unsigned char *noalloc_scratch()
 {
-    static unsigned char *addr[64] = {nullptr};
+    static std::atomic<unsigned char *> addr[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!addr[dev]) {
+    unsigned char *a = addr[dev].load(std::memory_order_acquire);
+    if (!a) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
-        addr[dev] = (unsigned char *)p;
+        a = (unsigned char *)p;
+        addr[dev].store(a, std::memory_order_release);
     }
-    return addr[dev];
+    return a;
 }
 
 } // namespace zdk

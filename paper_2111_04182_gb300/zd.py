@@ -152,6 +152,7 @@ def zd_morton_sort(keys: torch.Tensor, key_bits: int = 64, stream=None):
 
 
 ZD_NOALLOC_MAX_KEYS = 1 << 20
+ZD_MAX_KEYS = (1 << 30) - 1
 
 
 def zd_morton_sort_noalloc(keys: torch.Tensor, key_bits: int = 64, stream=None, out=None):
@@ -163,6 +164,12 @@ def zd_morton_sort_noalloc(keys: torch.Tensor, key_bits: int = 64, stream=None, 
     n = keys.numel()
     if out is None:
         out = (torch.empty_like(keys), torch.empty(n, dtype=torch.int32, device=keys.device))
+    else:
+        for t, dt, name in ((out[0], torch.int64, "out[0]"), (out[1], torch.int32, "out[1]")):
+            if not (isinstance(t, torch.Tensor) and t.dtype == dt and t.device == keys.device
+                    and t.is_contiguous() and t.numel() == n):
+                raise ValueError("%s must be a contiguous %s tensor of %d elements on %s"
+                                 % (name, dt, n, keys.device))
     _ok(_lib().zd_morton_sort_noalloc(_ptr(keys), n, key_bits, _ptr(out[0]), _ptr(out[1]),
                                       C.c_void_p(_stream(stream))), "zd_morton_sort_noalloc")
     return out

@@ -92,3 +92,30 @@ def test_bench_runs_the_oracle_only_for_the_cpu_baseline():
     funcs = re.split(r"\ndef ", text)
     users = [f.split("(")[0] for f in funcs if "from oracle import" in f or "import oracle" in f]
     assert users == ["cpu_baseline"], users
+
+
+def test_size_limits_rejected_on_the_host(lib):
+    """Sizes beyond ZD_MAX_KEYS (the radix sort's look-back words count a
+    digit's running total in 30 bits) return ZD_ERR_CAPACITY before any CUDA
+    call, so this runs without a GPU.  The device pointers are never touched."""
+    import ctypes as C
+    from paper_2111_04182_gb300 import zd
+    so = zd._lib()
+    fake = C.c_void_p(0x1000)
+    big = zd.ZD_MAX_KEYS + 1
+    assert so.zd_morton_sort(fake, big, 63, fake, fake, None, None) == zd.ZD_ERR_CAPACITY
+    p = zd.ZdParams(dim=3, leaf_size=16, coord_bits=21, coord_type=zd.ZD_COORD_I32)
+    h = C.c_void_p()
+    assert so.zd_build(C.byref(p), None, fake, big, None, C.byref(h)) == zd.ZD_ERR_CAPACITY
+    p.capacity = big
+    assert so.zd_build(C.byref(p), None, fake, 10, None, C.byref(h)) == zd.ZD_ERR_CAPACITY
+    assert not h.value
+    p.capacity = 0
+    off = (C.c_int64 * 2)(0, big)
+    assert so.zd_build_batched(C.byref(p), None, fake, off, fake, 1, None, C.byref(h)) == zd.ZD_ERR_CAPACITY
+    one = C.c_float(1.0)
+    # 2^27 * 8 pairs of (query, neighbour) > ZD_MAX_KEYS
+    assert so.zd_knn_dist_backward(fake, fake, fake, 1, 1 << 27, 16, 3, 8, C.byref(one), 0, fake, fake,
+                                   None) == zd.ZD_ERR_CAPACITY
+    assert so.zd_knn_dist_backward(fake, fake, fake, 1 << 40, 1 << 40, 16, 3, 8, C.byref(one), 0, fake,
+                                   fake, None) == zd.ZD_ERR_CAPACITY

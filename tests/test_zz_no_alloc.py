@@ -45,6 +45,10 @@ def test_noalloc_sort_matches_allocating_sort_twice(lib):
         (np.concatenate([rng.integers(0, 2 ** 63, size=zd.ZD_NOALLOC_MAX_KEYS - 4096, dtype=np.int64),
                          np.full(4096, 77, np.int64)]), 63),
         (rng.integers(0, 1 << 20, size=300_001, dtype=np.int64), 20),
+        # then larger again with all 64 bits (eight passes): the tile counters
+        # of this call sit inside the look-back words the earlier, smaller
+        # calls left behind, so those must be cleared before it starts
+        (rng.integers(-2 ** 63, 2 ** 63 - 1, size=zd.ZD_NOALLOC_MAX_KEYS - 777, dtype=np.int64), 64),
     ]
     for keys_np, bits in cases:
         keys = torch.from_numpy(keys_np).cuda()
@@ -69,3 +73,26 @@ def test_noalloc_sort_rejects_oversize_and_empty(lib):
     empty = torch.empty(0, dtype=torch.int64, device="cuda")
     assert _call_noalloc(zd, empty, 64, empty, torch.empty(0, dtype=torch.int32, device="cuda")) == zd.ZD_OK
     assert zd.zd_check() == zd.ZD_OK
+
+
+def test_noalloc_wrapper_with_caller_buffers(lib):
+    """The Python wrapper with caller-supplied outputs allocates nothing and
+    gives the allocating sort's result; mismatched outputs are refused on the
+    host before anything runs."""
+    zd = lib
+    rng = np.random.default_rng(7)
+    keys = torch.from_numpy(rng.integers(0, 1 << 40, size=65_537, dtype=np.int64)).cuda()
+    ref_k, ref_p = zd.zd_morton_sort(keys, 40)
+    out = (torch.empty_like(keys), torch.empty(keys.numel(), dtype=torch.int32, device="cuda"))
+    got = zd.zd_morton_sort_noalloc(keys, 40, out=out)
+    assert got[0] is out[0] and got[1] is out[1]
+    assert torch.equal(out[0], ref_k) and torch.equal(out[1], ref_p)
+    bad = [
+        (out[0][:-1], out[1]),                                  # too short
+        (out[0], out[1].to(torch.int64)),                       # wrong dtype
+        (out[0].view(-1, 1).expand(-1, 2)[:, 0], out[1]),       # not contiguous
+        (out[0].cpu(), out[1]),                                 # wrong device
+    ]
+    for b in bad:
+        with pytest.raises(ValueError):
+            zd.zd_morton_sort_noalloc(keys, 40, out=b)
