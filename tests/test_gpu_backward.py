@@ -1,6 +1,7 @@
 """GPU backward of a sum of k-NN distances against the fp64 oracle gradient
-(max relative error <= 1e-4 of the fp64 value) and finite differences, and
-the batched float forward against brute force with the fp64 ranking."""
+and finite differences, and the batched float forward against brute force
+with the fp64 ranking.  Gradient tolerance, per element:
+max_i |g_i - g64_i| / max(|g64_i|, 1e-3) <= 1e-4."""
 import numpy as np
 import pytest
 
@@ -22,7 +23,8 @@ def zd():
 
 
 def _rel(g, g64):
-    return np.max(np.abs(g - g64)) / max(np.max(np.abs(g64)), 1e-3)
+    """Largest per-element error relative to max(|g64_i|, 1e-3)."""
+    return float(np.max(np.abs(g.astype(np.float64) - g64) / np.maximum(np.abs(g64), 1e-3)))
 
 
 def test_backward_matches_fp64(zd, oracle):
@@ -93,3 +95,21 @@ def test_backward_is_deterministic_and_skips(zd):
                                      torch.ones(1, device=DEV))
     assert torch.allclose(gq, torch.tensor([[[-1.0, 0, 0]]], device=DEV))
     assert torch.allclose(gr[0, 0], torch.zeros(3, device=DEV))
+
+
+@pytest.mark.parametrize("scale", [1e-25, 1.0, 1e12])
+def test_backward_per_element_at_extreme_scales(zd, oracle, scale):
+    """The same clouds shrunk or blown up: the unit vectors do not depend on
+    the scale, so the per-element bound holds whether squared differences
+    would underflow or overflow in plain fp32."""
+    from paper_2111_04182_gb300 import datagen
+    rng = np.random.default_rng(12)
+    a, b = datagen.warped_pair(rng, 2000, 5000)
+    a, b = (a * scale).astype(np.float32), (b * scale).astype(np.float32)
+    idx, _ = oracle.knn_brute(b, 6, queries=a)
+    g = rng.standard_normal((2000, 6)).astype(np.float32)
+    gq, gr = zd.zd_knn_dist_backward(torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV),
+                                     torch.from_numpy(idx).to(DEV), torch.from_numpy(g).to(DEV))
+    _, ga, gb = oracle.knn_dist_grad(a, b, idx, g.astype(np.float64))
+    assert _rel(gq.cpu().numpy(), ga) <= 1e-4
+    assert _rel(gr.cpu().numpy(), gb) <= 1e-4

@@ -90,7 +90,7 @@ def test_noalloc_wrapper_with_caller_buffers(lib):
     bad = [
         (out[0][:-1], out[1]),                                  # too short
         (out[0], out[1].to(torch.int64)),                       # wrong dtype
-        (out[0].view(-1, 1).expand(-1, 2)[:, 0], out[1]),       # not contiguous
+        (torch.empty(2 * keys.numel(), dtype=torch.int64, device="cuda")[::2], out[1]),  # not contiguous
         (out[0].cpu(), out[1]),                                 # wrong device
     ]
     for b in bad:
