@@ -35,16 +35,49 @@ sys.path.insert(0, ROOT)
 METRIC = "kNN queries/s + zd-tree build pts/s (3D n=1e7,k=10) and % HBM roofline; fwd+bwd/s"
 
 # Algorithmic bytes (declared before measuring).
-#   all-points k-NN, per query: 12 (own coordinates) + 4 (sorted position ->
-#   id) + 12 (amortized node / leaf data) + 4k (ids) + 8k (int64 d^2).
-#   build, per point: encode 20, histogram 8, radix passes 20 + 24 (P - 1),
-#   gather 28, split 8, boxes 12, nodes 0.25 * 48.
-def knn_bytes_per_query(k: int) -> int:
-    return 12 + 4 + 12 + 12 * k
+#   all-points k-NN, per query: 4 dim (own coordinates) + 4 (sorted position
+#   -> id) + 12 (amortized node / leaf data) + 4k (ids) + 8k (int64 d^2; 4k
+#   for fp32 distances).
+#   build, per point (c = 4 dim coordinate bytes): encode c + 8, histogram 8,
+#   radix passes 20 + 24 (P - 1), gather 4 + 2c, split 8, boxes c, nodes
+#   0.25 * 48 (3D, 8 passes: 276).
+#   backward, per (query, neighbour): 12 (query) + 12 (reference, gathered)
+#   + 4 (id) + 12 (query gradient, amortized) + 12 (reference gradient).
+#   updates (paper-work model, Theorem 3): b (encode + sort + route, 276 B)
+#   + touched leaves * 2 * (L * 16 B) + rebuilt nodes * 48 B.
+def knn_bytes_per_query(k: int, dim: int = 3, dist_bytes: int = 8, own_id: bool = True) -> int:
+    return 4 * dim + (4 if own_id else 0) + 12 + (4 + dist_bytes) * k
 
 
-def build_bytes_per_point(passes: int = 8) -> int:
-    return 20 + 8 + (20 + 24 * (passes - 1)) + 28 + 8 + 12 + 12
+def build_bytes_per_point(passes: int = 8, dim: int = 3) -> int:
+    c = 4 * dim
+    return (c + 8) + 8 + (20 + 24 * (passes - 1)) + (4 + 2 * c) + 8 + c + 12
+
+
+def sort_passes(key_bits: int) -> int:
+    return (key_bits + 7) // 8
+
+
+BACKWARD_BYTES_PER_PAIR = 12 + 12 + 4 + 12 + 12
+
+
+def update_bytes(b: int, touched_leaves: int, leaf_size: int = 16, rebuilt_nodes: int = None) -> int:
+    """Paper-work model of one batch update (Theorem 3): the batch's encode,
+    sort and routing, the touched leaves read and written, and the nodes
+    rebuilt (one per touched leaf)."""
+    if rebuilt_nodes is None:
+        rebuilt_nodes = touched_leaves
+    return 276 * b + touched_leaves * 2 * leaf_size * 16 + rebuilt_nodes * 48
+
+
+def roofline(kernel: str, bytes_per_launch: float, ms: float, traffic=None, bound: str = "hbm") -> dict:
+    """Roofline object: algorithmic bytes of one launch over its measured
+    duration, against the measured HBM copy bandwidth."""
+    pk, pk_src = hbm_peak()
+    achieved = bytes_per_launch / (ms / 1e3) / 1e9
+    return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": pk, "peak_source": pk_src,
+            "unit": "GB/s", "frac": achieved / pk, "traffic": traffic,
+            "algorithmic_bytes_per_launch": int(bytes_per_launch)}
 
 
 def peaks() -> dict:
@@ -345,7 +378,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+        out["cpu_baseline"] = cpu_baseline("3d-clustered", w)
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
@@ -353,31 +386,111 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(w, sample: int) -> dict:
-    """The oracle (plain C, OpenMP over queries) on the host cores: a full
-    build plus leaf-based k-NN for `sample` sorted positions, scaled to the
-    whole step."""
+def cpu_baseline(kind: str, w: dict, **kw) -> dict:
+    """The oracle (plain C; OpenMP over independent queries only, its build
+    sequential) timed as it stands on the host cores, on a bounded sample of
+    workload `kind`; returns a cpu_baseline object in the unit of that
+    workload's line.  The only place this file runs the oracle."""
     from oracle import oracle
-    pts, k, L, B = w["pts"], w["k"], w["leaf_size"], w["coord_bits"]
-    n = len(pts)
     cores = len(os.sched_getaffinity(0))
-    t0 = time.perf_counter()
-    t = oracle.OracleTree(pts, L, B)
-    t_build = time.perf_counter() - t0
-    s = min(sample, n)
-    r0 = (n - s) // 2
-    t0 = time.perf_counter()
-    t.knn_sorted_range(k, r0, r0 + s, nthreads=cores)
-    t_knn = time.perf_counter() - t0
-    step = t_build + t_knn * n / s
-    return {"value": n / step, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": "full build of all %d points (1 thread) + leaf-based k-NN of %d consecutive sorted "
-                      "points (%d threads), k-NN time scaled by n/sample" % (n, s, cores),
-            "build_s": t_build, "knn_sample_s": t_knn}
+    base = {"cores": cores, "kind": "oracle"}
+    if kind in ("3d-clustered", "2d-uniform"):
+        # the whole step: build of all points + leaf-based k-NN of all points
+        pts, k, L, B = w["pts"], w["k"], w["leaf_size"], w["coord_bits"]
+        n = len(pts)
+        reps = kw.get("reps", 1)
+        tb, tk = [], []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            t = oracle.OracleTree(pts, L, B)
+            t1 = time.perf_counter()
+            t.knn(k, nthreads=cores)
+            t2 = time.perf_counter()
+            del t
+            tb.append(t1 - t0)
+            tk.append(t2 - t1)
+        b_s, k_s = float(np.median(tb)), float(np.median(tk))
+        return dict(base, value=n / (b_s + k_s), unit="queries/s",
+                    sample="the whole step: build of all %d points (1 thread) + leaf-based k-NN of all %d "
+                           "points (%d threads)%s" % (n, n, cores, ", median of %d" % reps if reps > 1 else ""),
+                    build_s=b_s, knn_s=k_s, build_pts_per_s=n / b_s, knn_queries_per_s=n / k_s)
+    if kind == "dynamic":
+        # one round on the live set the GPU ended with: the oracle's update is
+        # a rebuild of the current set (insert, then delete), then the round's
+        # bit-based queries
+        pts, ids, ins, dele, q, k = kw["pts"], kw["ids"], kw["ins"], kw["dele"], kw["queries"], w["k"]
+        L, B = w["leaf_size"], w["coord_bits"]
+        new_ids = np.arange(kw["next_id"], kw["next_id"] + len(ins), dtype=np.int32)
+        t0 = time.perf_counter()
+        t = oracle.OracleTree(np.concatenate([pts, ins]), L, B, ids=np.concatenate([ids, new_ids]))
+        t_ins = time.perf_counter() - t0
+        del t
+        all_pts, all_ids = np.concatenate([pts, ins]), np.concatenate([ids, new_ids])
+        keep = ~np.isin(all_ids, dele)
+        t0 = time.perf_counter()
+        t = oracle.OracleTree(all_pts[keep], L, B, ids=all_ids[keep])
+        t_del = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        t.knn(k, queries=q, mode=oracle.MODE_BIT, nthreads=cores)
+        t_q = time.perf_counter() - t0
+        del t
+        b = len(ins)
+        return dict(base, value=b / t_ins, unit="updates/s", insert_per_s=b / t_ins, delete_per_s=len(dele) / t_del,
+                    query_per_s=len(q) / t_q,
+                    sample="one round: rebuild of the live set after inserting %d points (%d points) and after "
+                           "deleting %d ids (1 thread), %d bit-based queries k=%d (%d threads)"
+                           % (b, len(all_pts), len(dele), len(q), k, cores),
+                    insert_s=t_ins, delete_s=t_del, query_s=t_q)
+    if kind == "batched":
+        off, pts, k, B = w["offsets"], w["pts"], w["k"], w["coord_bits"]
+        L, c_s = kw["leaf_size"], kw.get("clouds", 64)
+        t0 = time.perf_counter()
+        for c in range(c_s):
+            oracle.OracleTree(pts[off[c]:off[c + 1]], L, B).knn(k, nthreads=cores)
+        ts = time.perf_counter() - t0
+        frac = float(off[c_s]) / float(off[-1])
+        step = ts / frac
+        return dict(base, value=(len(off) - 1) / step, unit="clouds/s", points_per_s=float(off[-1]) / step,
+                    sample="the first %d clouds (%d points): per-cloud build (1 thread) + all-points k=%d "
+                           "(%d threads), time scaled by total/sampled points" % (c_s, int(off[c_s]), k, cores),
+                    sample_s=ts)
+    if kind == "differentiable":
+        # a few pairs: float tree of B, root-based k-NN of A (fp64 ranking),
+        # fp64 gradient; the GPU's outputs for those pairs are compared with
+        # the oracle's (FP32 error against FP64, per element)
+        A, Bc, k, L, B = w["A"], w["B"], w["k"], w["leaf_size"], w["coord_bits"]
+        gpu = kw["gpu"]  # {pair: (idx, dist, gA, gB)} host arrays
+        errs = {"dist_max_rel": 0.0, "grad_a_max_rel": 0.0, "grad_b_max_rel": 0.0, "ids_equal": True}
+        t0 = time.perf_counter()
+        outs = {}
+        for p in gpu:
+            lo, scale = oracle.quantization_of(Bc[p], B)
+            t = oracle.OracleTree(Bc[p], L, B, qlo=lo, qscale=scale)
+            oi, od = t.knn(k, queries=A[p], mode=oracle.MODE_ROOT, nthreads=cores)
+            _, ga, gb = oracle.knn_dist_grad(A[p], Bc[p], oi)
+            outs[p] = (oi, np.sqrt(od), ga, gb)
+        ts = time.perf_counter() - t0
+        for p, (oi, d64, ga, gb) in outs.items():
+            gi, gd, gA, gB = gpu[p]
+            errs["ids_equal"] &= bool(np.array_equal(gi, oi))
+            errs["dist_max_rel"] = max(errs["dist_max_rel"], float(np.max(np.abs(gd - d64) / d64)))
+            errs["grad_a_max_rel"] = max(errs["grad_a_max_rel"], float(np.max(
+                np.abs(gA - ga) / np.maximum(np.abs(ga), 1e-3))))
+            errs["grad_b_max_rel"] = max(errs["grad_b_max_rel"], float(np.max(
+                np.abs(gB - gb) / np.maximum(np.abs(gb), 1e-3))))
+        step = ts / len(gpu) * len(A)
+        return dict(base, value=1.0 / step, unit="fwd+bwd/s",
+                    sample="%d of %d pairs: float tree of B (1 thread), root-based k=%d of A (%d threads), fp64 "
+                           "gradient; time scaled by pairs" % (len(gpu), len(A), k, cores),
+                    sample_s=ts, fp32_vs_fp64=errs)
+    raise ValueError(kind)
 
 
 # ------------------------------------------------------------- reference
 def run_reference(args):
+    """The oracle as the reference arm: every step is the whole headline step
+    (build of all points + leaf-based k-NN of all points) run on the host
+    cores; the line reports the measured wall time per step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -388,15 +501,18 @@ def run_reference(args):
     w = datagen.workload_3d_clustered(n=args.n)
     n = len(w["pts"])
     for _ in range(args.warmup):  # untimed
-        cpu_baseline(w, args.cpu_sample)
-    vals = []
+        cpu_baseline("3d-clustered", w)
+    step_s = []
     for _ in range(args.steps):
-        cb = cpu_baseline(w, args.cpu_sample)
-        vals.append(cb["value"])
-    value = float(np.median(vals))
+        t0 = time.perf_counter()
+        cb = cpu_baseline("3d-clustered", w)
+        step_s.append(time.perf_counter() - t0)
+    mean_s = float(np.mean(step_s))
+    value = n / mean_s
     cb["value"] = value
+    cb["sample"] = "every step is the whole step: " + cb["sample"].split(": ", 1)[1]
     out = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": n / value * 1e3, "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
            "config": headline_config(n, w["k"], w["leaf_size"], w["coord_bits"], "host cores (oracle)",
                                      "n/a (host)"),
@@ -452,17 +568,47 @@ def bench_2d(args):
         ms.append((a.elapsed_time(b), b.elapsed_time(c)))
     assert zd.zd_check() == 0
     bm = float(np.median([m[0] for m in ms])); km = float(np.median([m[1] for m in ms]))
-    return {"workload": "2d-uniform-1e5", "metric": "queries/s (build + all-points k=10)",
-            "value": n / ((bm + km) / 1e3), "unit": "queries/s", "build_ms": bm, "knn_ms": km,
-            "build_pts_per_s": n / (bm / 1e3), "knn_queries_per_s": n / (km / 1e3), "steps": args.steps}
+    passes = sort_passes(2 * w["coord_bits"])
+    out = {"workload": "2d-uniform-1e5", "metric": "queries/s (build + all-points k=10)",
+           "value": n / ((bm + km) / 1e3), "unit": "queries/s", "build_ms": bm, "knn_ms": km,
+           "build_pts_per_s": n / (bm / 1e3), "knn_queries_per_s": n / (km / 1e3), "steps": args.steps,
+           "l2": "inputs and outputs (13 MB) fit in L2",
+           "roofline": roofline("k_knn_group<2,10,fs>", knn_bytes_per_query(k, dim=2) * n, km),
+           "build_roofline": roofline("build (%d sort passes)" % passes,
+                                      build_bytes_per_point(passes, dim=2) * n, bm)}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline("2d-uniform", w, reps=5)
+    return out
+
+
+def touched_leaves(tree, coord_bits: int, ins_pts=None, del_ids=None) -> int:
+    """Leaves of `tree` (before an update) that a batch touches: the leaf
+    each inserted key falls into by sorted position, or the leaf of each
+    deleted id.  Counted with torch on the device, outside any timed region,
+    for the paper-work byte model of an update."""
+    import torch
+    from paper_2111_04182_gb300 import zd
+    e = tree.export()
+    leaf_lo = e["leaf_lo"].to(torch.int64)
+    if ins_pts is not None:
+        pos = torch.searchsorted(e["keys"], zd.zd_morton_encode(ins_pts, coord_bits))
+    else:
+        ids = e["ids"].to(torch.int64)
+        inv = torch.full((int(ids.max()) + 1,), -1, dtype=torch.int64, device=ids.device)
+        inv[ids] = torch.arange(len(ids), device=ids.device)
+        pos = inv[del_ids.to(torch.int64)]
+    leaf = torch.searchsorted(leaf_lo[1:], pos, right=True).clamp_(max=len(leaf_lo) - 2)
+    return int(torch.unique(leaf).numel())
 
 
 def bench_dynamic(args):
     """5e7 uniform points; rounds of +1e6 insert, -1e6 delete, 1e6 queries
     (k = 5, bit-based).  Every round, sampled rows are checked for properties
     any exact answer has (live ids, distances recomputed from the host copy of
-    the points, non-decreasing rows); exactness against the oracle is the job
-    of the full-size tests."""
+    the points, non-decreasing rows); every row of every round is checked
+    against the oracle by the full-size tests.  Rooflines: updates by the
+    paper-work model (Theorem 3, touched leaves counted per round), queries
+    by the external-query search bytes."""
     import torch
     from paper_2111_04182_gb300 import datagen, zd
     rounds = args.rounds
@@ -475,14 +621,17 @@ def bench_dynamic(args):
     a.record(); t = zd.zd_build(pts, w.leaf_size, w.coord_bits, capacity=cap); b.record(); b.synchronize()
     build_ms = a.elapsed_time(b)
     del pts
-    ins_ms, del_ms, q_ms, checked = [], [], [], 0
+    ins_ms, del_ms, q_ms, checked, t_ins, t_del = [], [], [], 0, [], []
     rng = np.random.default_rng(7)
     for r in range(rounds):
         ins, dele, q = w.round()
         ins_d, del_d, q_d = torch.from_numpy(ins).cuda(), torch.from_numpy(dele).cuda(), torch.from_numpy(q).cuda()
+        t_ins.append(touched_leaves(t, w.coord_bits, ins_pts=ins_d))
         torch.cuda.synchronize()
         e = _events(6)
-        e[0].record(); new = t.insert(ins_d); e[1].record()
+        e[0].record(); new = t.insert(ins_d); e[1].record(); e[1].synchronize()
+        t_del.append(touched_leaves(t, w.coord_bits, del_ids=del_d))
+        torch.cuda.synchronize()
         e[2].record(); t.delete(del_d); e[3].record()
         e[4].record(); idx, d2 = t.knn(w.k, queries=q_d, mode=zd.ZD_SEARCH_BIT); e[5].record()
         e[5].synchronize()
@@ -497,11 +646,29 @@ def bench_dynamic(args):
         checked += len(sel)
     assert zd.zd_check() == 0
     im, dm, qm = (float(np.median(x)) for x in (ins_ms, del_ms, q_ms))
+    ti, td = float(np.mean(t_ins)), float(np.mean(t_del))
     t.free()
-    return {"workload": "dynamic-5e7", "metric": "updates/s (insert, delete) and queries/s", "unit": "updates/s",
-            "value": w.batch / (im / 1e3), "insert_per_s": w.batch / (im / 1e3), "delete_per_s": w.batch / (dm / 1e3),
-            "query_per_s": w.batch / (qm / 1e3), "insert_ms": im, "delete_ms": dm, "query_ms": qm,
-            "initial_build_ms": build_ms, "rounds": rounds, "property_checked_rows": checked, "k": w.k}
+    qbytes = (12 + 8 + 24 * sort_passes(3 * w.coord_bits) + 16 + knn_bytes_per_query(w.k, own_id=False)) * w.batch
+    out = {"workload": "dynamic-5e7", "metric": "updates/s (insert, delete) and queries/s", "unit": "updates/s",
+           "value": w.batch / (im / 1e3), "insert_per_s": w.batch / (im / 1e3),
+           "delete_per_s": w.batch / (dm / 1e3), "query_per_s": w.batch / (qm / 1e3), "insert_ms": im,
+           "delete_ms": dm, "query_ms": qm, "initial_build_ms": build_ms, "rounds": rounds,
+           "property_checked_rows": checked, "k": w.k, "touched_leaves": {"insert": ti, "delete": td},
+           "roofline": roofline("insert (merge + re-derive)", update_bytes(w.batch, int(ti), w.leaf_size), im),
+           "rooflines": {
+               "delete": roofline("delete (mark + compact + re-derive)", update_bytes(w.batch, int(td), w.leaf_size), dm),
+               "query": roofline("queries (encode + sort + k_knn)", qbytes, qm)},
+           "byte_models": "updates: 276 B per batch point + 2 * L * 16 B per touched leaf + 48 B per rebuilt "
+                          "node (one per touched leaf); queries: encode 20 + sort 24/pass + gather 16 + search "
+                          "12 + 12 + 12k per query"}
+    if not args.no_cpu_baseline:
+        live = w.live
+        ins, dele, q = w.round()
+        out["cpu_baseline"] = cpu_baseline("dynamic", {"k": w.k, "leaf_size": w.leaf_size,
+                                                       "coord_bits": w.coord_bits},
+                                           pts=all_pts[live], ids=live.astype(np.int32), ins=ins, dele=dele,
+                                           queries=q, next_id=int(w.n0 + rounds * w.batch))
+    return out
 
 
 def bench_batched(args):
@@ -555,49 +722,97 @@ def bench_batched(args):
             step()
         b.record(); b.synchronize()
         ms.append(a.elapsed_time(b))
+    # the same step eagerly with events between the phases, for the rooflines
+    ph = []
+    for _ in range(max(1, args.steps // 2)):
+        a, b, c = _events(3)
+        a.record(); t = zd.zd_build_batched(pts, off, L, B, offsets_device=off_d); b.record()
+        zd.zd_knn_batched(t, k, out=(idx, d2), mapping=mp); c.record(); c.synchronize(); t.free()
+        ph.append((a.elapsed_time(b), b.elapsed_time(c)))
     assert zd.zd_check() == 0
     m = float(np.median(ms))
+    bm, km = float(np.median([x[0] for x in ph])), float(np.median([x[1] for x in ph]))
+    cbits = int(np.ceil(np.log2(len(off) - 1)))
+    passes = sort_passes(3 * B + cbits)
     out = {"workload": "batched-4096", "metric": "clouds/s, points/s (build + all-points k=16 per cloud)",
            "value": (len(off) - 1) / (m / 1e3), "unit": "clouds/s", "ms_per_step": m,
            "points_per_s": n / (m / 1e3), "queries_per_s": n / (m / 1e3), "n_points": n, "k": k,
            "leaf_size": L, "mapping": tune["mapping_name"], "tuning": tune["table"],
-           "graph": graph is not None, "graph_launches_per_step": 1 if graph is not None else None}
+           "graph": graph is not None, "graph_launches_per_step": 1 if graph is not None else None,
+           "eager_phase_ms": {"build": bm, "knn": km},
+           "l2": "inputs (1.6 GB) and outputs (26 GB) exceed L2",
+           "roofline": roofline("k_knn (forest, %s)" % tune["mapping_name"], knn_bytes_per_query(k) * n, km),
+           "build_roofline": roofline("forest build (%d sort passes)" % passes,
+                                      build_bytes_per_point(passes) * n, bm),
+           "step_roofline": roofline("graph: forest build + k-NN", (build_bytes_per_point(passes) +
+                                                                   knn_bytes_per_query(k)) * n, m)}
     if graph is None:
         out["graph_error"] = graph_error
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline("batched", w, leaf_size=L)
     return out
 
 
 def bench_differentiable(args):
     """64 pairs of float clouds (A 16384, B 32768): k = 8 neighbours in B for
     every point of A (fp64 ranking), loss = sum of fp32 distances, backward to
-    A and B."""
+    A and B.  The CPU baseline also reports the FP32 distances' and
+    gradients' largest per-element errors against the oracle's FP64 values on
+    its sample pairs."""
     import torch
     from paper_2111_04182_gb300 import datagen, zd
     w = datagen.workload_differentiable()
     A = torch.from_numpy(w["A"]).cuda().requires_grad_(True)
     B = torch.from_numpy(w["B"]).cuda().requires_grad_(True)
     k = w["k"]
+    P, m, r = w["A"].shape[0], w["A"].shape[1], w["B"].shape[1]
 
-    def step():
+    def step(ev=None):
         A.grad = None
         B.grad = None
+        if ev:
+            ev[0].record()
         dist, idx = zd.KnnDist.apply(A, B, k, w["leaf_size"], w["coord_bits"])
-        dist.sum().backward()
-        return idx
+        loss = dist.sum()
+        if ev:
+            ev[1].record()
+        loss.backward()
+        if ev:
+            ev[2].record()
+        return dist, idx
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     ms = []
     for _ in range(args.steps):
-        a, b = _events(2)
-        a.record(); idx = step(); b.record(); b.synchronize()
-        ms.append(a.elapsed_time(b))
+        ev = _events(3)
+        dist, idx = step(ev)
+        ev[2].synchronize()
+        ms.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
     assert zd.zd_check() == 0
-    m = float(np.median(ms))
-    return {"workload": "differentiable-64x16384x32768", "metric": "fwd+bwd/s", "value": 1e3 / m,
-            "unit": "fwd+bwd/s", "ms_per_step": m, "pairs_per_s": 64 * 1e3 / m, "queries_per_s": 64 * 16384 * 1e3 / m,
-            "k": k}
+    fm, bm = float(np.median([x[0] for x in ms])), float(np.median([x[1] for x in ms]))
+    mm = fm + bm
+    pairs = P * m * k
+    # forward: forest of B (quantize + build, 8 passes) + external queries
+    # (encode + sort + gather of A) + the search writing ids and fp32 distances
+    fwd_bytes = (build_bytes_per_point(8) * P * r +
+                 (20 + 24 * 8 + 16 + knn_bytes_per_query(k, dist_bytes=4, own_id=False)) * P * m)
+    out = {"workload": "differentiable-64x16384x32768", "metric": "fwd+bwd/s", "value": 1e3 / mm,
+           "unit": "fwd+bwd/s", "ms_per_step": mm, "forward_ms": fm, "backward_ms": bm,
+           "pairs_per_s": P * 1e3 / mm, "queries_per_s": P * m * 1e3 / mm, "k": k,
+           "roofline": roofline("forward (forest build + k_knn_group_f)", fwd_bytes, fm),
+           "backward_roofline": roofline("backward (k_grad_q + pair sort + k_grad_ref)",
+                                         BACKWARD_BYTES_PER_PAIR * pairs, bm)}
+    if not args.no_cpu_baseline:
+        sample = (0, 37)
+        gpu = {p: (idx[p].cpu().numpy(), dist[p].detach().cpu().numpy().astype(np.float64),
+                   A.grad[p].cpu().numpy().astype(np.float64), B.grad[p].cpu().numpy().astype(np.float64))
+               for p in sample}
+        out["cpu_baseline"] = cpu_baseline("differentiable", w, gpu=gpu)
+        out["fp32_vs_fp64"] = dict(out["cpu_baseline"]["fp32_vs_fp64"], pairs=list(sample),
+                                   form="max_i |x_i - x64_i| / max(|x64_i|, 1e-3) (distances: / x64_i)")
+    return out
 
 
 def bench_skewed(args):
@@ -836,7 +1051,6 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d-clustered")
     ap.add_argument("--n", type=int, default=10_000_000)
-    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rounds", type=int, default=20)
     ap.add_argument("--dyn-n0", type=int, default=50_000_000)

@@ -26,7 +26,13 @@ def test_headline_config_keys(bench):
 def test_algorithmic_bytes(bench):
     assert bench.knn_bytes_per_query(10) == 148
     assert bench.knn_bytes_per_query(100) == 1228
-    assert 250 <= bench.build_bytes_per_point() <= 300
+    assert bench.build_bytes_per_point() == 276
+    assert bench.knn_bytes_per_query(10, dim=2) == 144
+    assert bench.knn_bytes_per_query(8, dist_bytes=4, own_id=False) == 24 + 64
+    assert bench.sort_passes(63) == 8 and bench.sort_passes(40) == 5 and bench.sort_passes(64) == 8
+    assert bench.update_bytes(1, 1) == 276 + 512 + 48
+    r = bench.roofline("k", 2e9, 1.0)
+    assert abs(r["achieved"] - 2000.0) < 1e-9 and abs(r["frac"] - 2000.0 / r["peak"]) < 1e-12
 
 
 def test_profiled_traffic_follows_the_sources(bench, tmp_path, monkeypatch):
@@ -61,9 +67,12 @@ def test_reference_arm_prints_one_json_line():
     import json
     import subprocess
     import sys
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--n", "20000", "--cpu-sample", "5000"],
+    import time
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "3",
+                        "--warmup", "0", "--n", "20000"],
                        capture_output=True, text=True, timeout=300, cwd=ROOT)
+    wall = time.perf_counter() - t0
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -73,3 +82,6 @@ def test_reference_arm_prints_one_json_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    # the reported time per step is a measured one: the steps fit in the run
+    assert d["ms_per_step"] * d["steps"] / 1e3 <= wall
+    assert abs(d["value"] - 20000 / (d["ms_per_step"] / 1e3)) <= 1e-6 * d["value"]
