@@ -53,9 +53,12 @@ typedef enum zd_status {
     ZD_ERR_DUPLICATE_ID = 6, /* the same id twice in one delete batch */
     ZD_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
     ZD_ERR_UNIMPLEMENTED = 8,/* a parameter combination not built (e.g. k > ZD_MAX_K) */
-    ZD_ERR_CAPACITY = 9      /* beyond a size limit: an insert past the tree's
+    ZD_ERR_CAPACITY = 9,     /* beyond a size limit: an insert past the tree's
                                 capacity, or more than ZD_MAX_KEYS keys (or
                                 ZD_NOALLOC_MAX_KEYS for the no-allocation sort) */
+    ZD_ERR_INTERNAL = 10     /* a kernel's index check failed (recorded only by
+                                a library built with -DZD_DEBUG; the access was
+                                skipped): a bug in the library */
 } zd_status;
 
 enum { ZD_COORD_I32 = 0, ZD_COORD_F32 = 1 };

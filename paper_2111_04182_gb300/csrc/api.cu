@@ -234,18 +234,31 @@ static int build_core(zd_tree *t, const void *d_pts, const int64_t *seg_off, int
     if (!raw.p || !perm.p || !hist.p || !mm.p) return ZD_ERR_OOM;
     ZD_CUDA(cudaMemsetAsync(hist.p, 0, MAX_PASSES * RADIX * sizeof(u32), s));
     const int cloud_shift = seg_off ? t->cloud_bit : 0;
-    if (t->is_float) {
-        ZD_TRY(launch_float_frames((const float *)d_pts, n, dim, t->B, seg_off, n_seg, max_seg,
-                                   t->frame, mm.p, s));
-        ZD_TRY(launch_encode_f32((const float *)d_pts, n, dim, t->B, t->frame, seg_off, n_seg,
-                                 cloud_shift, raw.p, hist.p, npasses, s));
-    } else {
-        ZD_TRY(launch_encode_i32((const int32_t *)d_pts, n, dim, t->B, t->p.shift, seg_off, n_seg,
-                                 cloud_shift, raw.p, hist.p, npasses, s));
+    {
+        NvtxScope r("encode");
+        if (t->is_float) {
+            ZD_TRY(launch_float_frames((const float *)d_pts, n, dim, t->B, seg_off, n_seg, max_seg,
+                                       t->frame, mm.p, s));
+            ZD_TRY(launch_encode_f32((const float *)d_pts, n, dim, t->B, t->frame, seg_off, n_seg,
+                                     cloud_shift, raw.p, hist.p, npasses, s));
+        } else {
+            ZD_TRY(launch_encode_i32((const int32_t *)d_pts, n, dim, t->B, t->p.shift, seg_off, n_seg,
+                                     cloud_shift, raw.p, hist.p, npasses, s));
+        }
     }
-    ZD_TRY(radix_sort(raw.p, n, t->key_bits, t->keys, perm.p, hist.p, m));
-    ZD_TRY(launch_gather(d_pts, dim, n, perm.p, t->keys, t->cloud_bit, t->cloud_off, 0, t->pts, s));
-    ZD_TRY(build_topology(t->keys, t->pts, n, t->p.leaf_size, dim, t->is_float, t->cloud_bit, topo_of(t), m));
+    {
+        NvtxScope r("sort");
+        ZD_TRY(radix_sort(raw.p, n, t->key_bits, t->keys, perm.p, hist.p, m));
+    }
+    {
+        NvtxScope r("gather");
+        ZD_TRY(launch_gather(d_pts, dim, n, perm.p, t->keys, t->cloud_bit, t->cloud_off, 0, t->pts, s));
+    }
+    {
+        NvtxScope r("topology");
+        ZD_TRY(build_topology(t->keys, t->pts, n, t->p.leaf_size, dim, t->is_float, t->cloud_bit, topo_of(t),
+                              m));
+    }
     return m.failed ? ZD_ERR_OOM : ZD_OK;
 }
 
@@ -287,7 +300,8 @@ const char *zd_status_string(int status)
     case ZD_ERR_DUPLICATE_ID: return "id repeated in one batch";
     case ZD_ERR_TIMEOUT: return "bounded device wait timed out";
     case ZD_ERR_UNIMPLEMENTED: return "not implemented for these parameters";
-    case ZD_ERR_CAPACITY: return "tree capacity exceeded";
+    case ZD_ERR_CAPACITY: return "size limit exceeded";
+    case ZD_ERR_INTERNAL: return "internal index check failed (debug build)";
     default: return "unknown status";
     }
 }
@@ -310,6 +324,7 @@ int zd_check(void *stream)
 int zd_morton_encode(const zd_params *p, const int32_t *d_pts, int64_t n, uint64_t *d_keys,
                      void *stream)
 {
+    NvtxScope nvtx_("zd_morton_encode");
     ZD_TRY(check_params(p));
     if (p->coord_type != ZD_COORD_I32 || n < 0 || (n > 0 && (!d_pts || !d_keys)))
         return ZD_ERR_INVALID_ARG;
@@ -321,6 +336,7 @@ int zd_morton_encode(const zd_params *p, const int32_t *d_pts, int64_t n, uint64
 int zd_morton_sort(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t *d_keys_out,
                    int32_t *d_perm_out, const zd_allocator *alloc, void *stream)
 {
+    NvtxScope nvtx_("zd_morton_sort");
     if (n < 0 || key_bits < 1 || key_bits > 64) return ZD_ERR_INVALID_ARG;
     if (n > 0 && (!d_keys_in || !d_keys_out || !d_perm_out)) return ZD_ERR_INVALID_ARG;
     if (n > ZD_MAX_KEYS) return ZD_ERR_CAPACITY;
@@ -336,6 +352,7 @@ int zd_morton_sort(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t 
 int zd_build(const zd_params *p, const zd_allocator *alloc, const void *d_pts, int64_t n,
              void *stream, zd_tree **out)
 {
+    NvtxScope nvtx_("zd_build");
     if (!out) return ZD_ERR_INVALID_ARG;
     *out = nullptr;
     ZD_TRY(check_params(p));
@@ -379,6 +396,7 @@ int zd_build_batched(const zd_params *p, const zd_allocator *alloc, const void *
                      const int64_t *h_offsets, const int64_t *d_offsets, int64_t n_clouds,
                      void *stream, zd_tree **out)
 {
+    NvtxScope nvtx_("zd_build_batched");
     if (!out) return ZD_ERR_INVALID_ARG;
     *out = nullptr;
     ZD_TRY(check_params(p));
@@ -434,6 +452,7 @@ int zd_build_batched(const zd_params *p, const zd_allocator *alloc, const void *
 
 int zd_free(zd_tree *t, void *stream)
 {
+    NvtxScope nvtx_("zd_free");
     if (!t) return ZD_OK;
     tree_release(t, (cudaStream_t)stream);
     free(t);
@@ -502,6 +521,7 @@ extern "C" int zd_export_tree(const zd_tree *t, int32_t *d_ids, uint64_t *d_keys
                               int32_t *d_leaf_parent, void *d_node_box_lo, void *d_node_box_hi,
                               void *d_leaf_box_lo, void *d_leaf_box_hi, void *stream)
 {
+    NvtxScope nvtx_("zd_export_tree");
     if (!t) return ZD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int nl = 1;
@@ -540,6 +560,7 @@ extern "C" int zd_export_tree(const zd_tree *t, int32_t *d_ids, uint64_t *d_keys
 static int prepare_queries(const zd_tree *t, const void *d_q, int64_t m, const int64_t *seg_off,
                            int64_t n_seg, Mem &mem, u64 *qkeys, int4 *q4)
 {
+    NvtxScope r("prepare queries");
     cudaStream_t s = mem.s;
     const int npasses = (t->key_bits + RADIX_BITS - 1) / RADIX_BITS;
     Scratch<u64> raw(mem, m);
@@ -562,6 +583,7 @@ static int prepare_queries(const zd_tree *t, const void *d_q, int64_t m, const i
 static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m, int k, int mode,
                    int32_t *d_idx, void *d_dist, cudaStream_t s, const int64_t *d_qoff = nullptr)
 {
+    NvtxScope r("search");
     const int variant = mode & (ZD_KNN_THREAD_PER_QUERY | ZD_KNN_WARP_GROUP);
     mode &= 0xff;
     KnnArgs a;
@@ -633,6 +655,7 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
 extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k, int mode,
                       int32_t *d_idx, void *d_dist, void *stream)
 {
+    NvtxScope nvtx_("zd_knn");
     if (!t || !d_idx || k < 1) return ZD_ERR_INVALID_ARG;
     if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
     if (t->cloud_off) return ZD_ERR_INVALID_ARG; // forests: zd_knn_batched
@@ -661,6 +684,7 @@ extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k,
 extern "C" int zd_knn_batched(const zd_tree *t, const void *d_queries, const int64_t *d_query_offsets,
                               int64_t m, int k, int mode_flags, int32_t *d_idx, void *d_dist, void *stream)
 {
+    NvtxScope nvtx_("zd_knn_batched");
     if (!t || !d_idx || k < 1) return ZD_ERR_INVALID_ARG;
     if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
     if (!t->cloud_off) return ZD_ERR_INVALID_ARG;
@@ -695,6 +719,7 @@ int update_live_bits(u32 *live, int64_t a, int64_t z, int set, cudaStream_t s);
 
 extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t *d_new_ids, void *stream)
 {
+    NvtxScope nvtx_("zd_insert_batch");
     if (!t || b < 0 || (b > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
     if (t->cloud_off || t->is_float) return ZD_ERR_UNIMPLEMENTED;
     if (b == 0) return ZD_OK;
@@ -740,6 +765,7 @@ extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t
 
 extern "C" int zd_delete_batch(zd_tree *t, const int32_t *d_ids, int64_t b, void *stream)
 {
+    NvtxScope nvtx_("zd_delete_batch");
     if (!t || b < 0 || (b > 0 && !d_ids)) return ZD_ERR_INVALID_ARG;
     if (t->cloud_off || t->is_float) return ZD_ERR_UNIMPLEMENTED;
     if (b == 0) return ZD_OK;
@@ -771,6 +797,7 @@ extern "C" int zd_knn_dist_backward(const float *d_q, const float *d_ref, const 
                                     const float *d_gout, int gout_per_pair, float *d_gq,
                                     float *d_gref, void *stream)
 {
+    NvtxScope nvtx_("zd_knn_dist_backward");
     if (batch < 0 || m < 0 || r < 0 || k < 1 || (dim != 2 && dim != 3)) return ZD_ERR_INVALID_ARG;
     // (each factor is bounded first so that the products cannot overflow)
     if (batch > ZD_MAX_KEYS || m > ZD_MAX_KEYS || r > ZD_MAX_KEYS || k > ZD_MAX_K ||

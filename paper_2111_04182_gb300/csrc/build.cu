@@ -25,11 +25,12 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t *__restrict__ pts,
                                                 const int32_t *__restrict__ perm,
                                                 const u64 *__restrict__ keys, int cloud_bit,
                                                 const int64_t *__restrict__ cloud_off,
-                                                int32_t base_id, int4 *__restrict__ out)
+                                                int32_t base_id, int4 *__restrict__ out, u32 *status)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t src = perm[i];
+        if (!ZD_DCHECK(src >= 0 && src < n, status)) continue;
         int4 r;
         r.x = pts[src * DIM + 0];
         r.y = pts[src * DIM + 1];
@@ -48,10 +49,10 @@ int launch_gather(const void *pts_in, int dim, int64_t n, const int32_t *perm,
     unsigned g = grid_for(n, 256, 152 * 32);
     if (dim == 3)
         k_gather<3><<<g, 256, 0, s>>>((const int32_t *)pts_in, n, perm, sorted_keys, cloud_bit,
-                                      cloud_off, base_id, pts_out);
+                                      cloud_off, base_id, pts_out, status_word());
     else
         k_gather<2><<<g, 256, 0, s>>>((const int32_t *)pts_in, n, perm, sorted_keys, cloud_bit,
-                                      cloud_off, base_id, pts_out);
+                                      cloud_off, base_id, pts_out, status_word());
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(256) k_internal(const u64 *__restrict__ keys,
                                                   const int *__restrict__ meta, int64_t max_nodes,
                                                   int2 *__restrict__ ichild, int *__restrict__ iparent,
                                                   int *__restrict__ ibit, int2 *__restrict__ irange,
-                                                  int *__restrict__ lparent)
+                                                  int *__restrict__ lparent, u32 *status)
 {
     const int nl = meta[0];
     const int m = nl - 1; // internal nodes
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(256) k_internal(const u64 *__restrict__ keys,
         } while (t > 1);
         const int g = i + s * dn + min(dn, 0);
         const int a = min(i, j), b = max(i, j);
+        if (!ZD_DCHECK(a >= 0 && b < nl && a <= g && g < b, status)) continue;
         const int left = (a == g) ? ~g : g;
         const int right = (b == g + 1) ? ~(g + 1) : g + 1;
         ichild[i] = make_int2(left, right);
@@ -342,7 +344,8 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
                                                const int2 *__restrict__ ichild,
                                                const int *__restrict__ iparent,
                                                const int *__restrict__ lparent, int4 *ibox,
-                                               int4 *lbox, int *counter, float4 *fibox, float4 *flbox)
+                                               int4 *lbox, int *counter, float4 *fibox, float4 *flbox,
+                                               u32 *status)
 {
     typedef BoxOps<FLOAT> B;
     const int nl = meta[0];
@@ -368,6 +371,7 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
         }
         int p = lparent[j];
         while (p >= 0) {
+            if (!ZD_DCHECK(p < nl - 1, status)) break;
             // acq_rel: publishes this thread's boxes, and the second arriver
             // sees its sibling's
             if (atomic_add_acq_rel(&counter[p], 1) == 0) break; // the sibling finishes this node
@@ -486,18 +490,18 @@ int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, i
     const int64_t max_nodes = n > 1 ? n - 1 : 1;
     k_internal<<<grid_for(max_nodes, 256, 152 * 64), 256, 0, s>>>(keys, b.leaf_lo, b.meta, max_nodes,
                                                                  b.ichild, b.iparent, b.ibit, b.irange,
-                                                                 b.lparent);
+                                                                 b.lparent, status_word());
     ZD_CUDA(cudaGetLastError());
     ZD_CUDA(cudaMemsetAsync(b.counter, 0, sizeof(int) * (size_t)max_nodes, s));
     const int64_t max_leaves = n > 0 ? n : 1;
     if (is_float)
         k_boxes<true><<<grid_for(max_leaves, 256, 152 * 64), 256, 0, s>>>(
             pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter,
-            nullptr, nullptr);
+            nullptr, nullptr, status_word());
     else
         k_boxes<false><<<grid_for(max_leaves, 256, 152 * 64), 256, 0, s>>>(
             pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter,
-            b.fibox, b.flbox);
+            b.fibox, b.flbox, status_word());
     if (!is_float && b.fpts && n > 0)
         k_fpts<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(pts, n, b.fpts);
     ZD_CUDA(cudaGetLastError());

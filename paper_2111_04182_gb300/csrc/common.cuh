@@ -15,11 +15,22 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/zd.h"
 
 namespace zdk {
+
+// Host: an NVTX range over a scope, so a profiler's timeline shows every
+// entry point and its phases (encode, sort, gather, topology, search, ...).
+// With no tool attached a range costs one call.
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 typedef unsigned long long u64;
 typedef unsigned int u32;
@@ -33,6 +44,17 @@ __device__ __forceinline__ void set_status(u32 *status, int code)
 
 // Host: address of this device's status word (looked up once per device).
 u32 *status_word();
+
+// Debug builds (compiled with -DZD_DEBUG) check the index arithmetic of the
+// kernels before the accesses it guards: a failed check records
+// ZD_ERR_INTERNAL in the status word and evaluates to false, and the caller
+// skips the access (never a trap, so the context stays usable).  In normal
+// builds the check is the constant true and costs nothing.
+#ifdef ZD_DEBUG
+#define ZD_DCHECK(cond, status) ((cond) ? true : (::zdk::set_status((status), ZD_ERR_INTERNAL), false))
+#else
+#define ZD_DCHECK(cond, status) true
+#endif
 
 __device__ __forceinline__ unsigned long long globaltimer()
 {

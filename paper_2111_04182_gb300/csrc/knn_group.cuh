@@ -221,6 +221,7 @@ __device__ __forceinline__ void group_search(const TreeView &t, int start, int l
     int sp = 0;
     int v = start;
     while (true) {
+        if (!ZD_DCHECK(node_in_range(t, v), status)) return;
         // the nearer child is searched next directly; the farther one waits
         // on the stack (lane 0 writes it, every lane holds the same pointer)
         if (!(v < 0 && ~v >= l0 && ~v <= l1)) { // else scanned already
@@ -300,6 +301,7 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
             (__ldg(t.keys + __ldg(t.leaf_lo + l1)) >> t.cloud_bit) != cloud)
             return;
     }
+    if (!ZD_DCHECK(l0 >= 0 && l0 <= l1 && node_in_range(t, ~l1), status)) return;
     const int P0 = __ldg(t.leaf_lo + l0), P1 = __ldg(t.leaf_lo + l1 + 1);
     if (FS) group_scan_f<DIM, K>(t, P0, P1, c, key, thr, thr_f);
     else group_scan<DIM, K>(t, P0, P1, c, key, thr);

@@ -148,6 +148,7 @@ __device__ __forceinline__ void group_search_ff(const TreeView &t, int start, in
     int sp = 0;
     int v = start;
     while (true) {
+        if (!ZD_DCHECK(node_in_range(t, v), status)) return;
         // the nearer child is searched next directly; the farther one waits
         // on the stack (lane 0 writes it, every lane holds the same pointer)
         if (!(v < 0 && ~v >= l0 && ~v <= l1)) { // else scanned already

@@ -243,6 +243,14 @@ __device__ __forceinline__ void scan_leaf(const TreeView &t, int leaf, int self,
     }
 }
 
+// Node v names an existing node: internal 0 <= v < n_leaves - 1, or leaf
+// ~v < n_leaves (debug-build check).
+__device__ __forceinline__ bool node_in_range(const TreeView &t, int v)
+{
+    const int nl = __ldg(t.meta);
+    return v < 0 ? (~v < nl) : (v < nl - 1);
+}
+
 __device__ __forceinline__ void node_box(const TreeView &t, int v, int4 &lo, int4 &hi)
 {
     const int4 *b = v < 0 ? t.lbox + 2 * (~v) : t.ibox + 2 * v;
@@ -285,6 +293,7 @@ __device__ __forceinline__ void search_down(const TreeView &t, int v, typename M
     int u = v;
     D du = dv;
     while (true) {
+        if (!ZD_DCHECK(node_in_range(t, u), status)) return;
         if (du <= bd[K - 1]) { // else pruned by the (possibly shrunk) k-th distance
             if (u < 0) {
                 scan_leaf<DIM, K, FLOAT>(t, ~u, self, q, pf, bd, bi);
@@ -390,6 +399,7 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
                 leaf = ~v;
             }
             // searchUp (Algorithm 3)
+            if (!ZD_DCHECK(node_in_range(t, ~leaf), status)) return;
             scan_leaf<DIM, K, FLOAT>(t, leaf, self, q, pf, bd, bi);
             int node = ~leaf;
             int par = __ldg(t.lparent + leaf);

@@ -323,6 +323,7 @@ struct WideQuery {
         int u = v;
         D du = dv;
         while (true) {
+            if (!ZD_DCHECK(node_in_range(t, u), status)) return false;
             if (du <= td) { // else pruned by the (possibly shrunk) k-th distance
                 if (u < 0) {
                     scan_leaf(~u);

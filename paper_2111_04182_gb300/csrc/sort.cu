@@ -464,6 +464,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(PassArgs a, int pass)
     for (int i = 0; i < SORT_ITEMS; ++i) {
         if (dg[i] < RADIX) {
             u32 pos = s_excl[dg[i]] + s_whist[warp * RADIX + dg[i]] + rk[i];
+            if (!ZD_DCHECK(pos < (u32)valid_count, a.status)) continue;
             s_keys[pos] = k[i];
             s_vals[pos] = v[i];
         }
@@ -474,6 +475,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(PassArgs a, int pass)
         u64 key = s_keys[j];
         int dj = (int)((key >> shift) & (RADIX - 1));
         u64 gpos = (u64)s_glob[dj] + (u64)(j - (int)s_excl[dj]);
+        if (!ZD_DCHECK(gpos < (u64)a.n, a.status)) continue;
         kdst[gpos] = key;
         vdst[gpos] = s_vals[j];
     }
@@ -602,6 +604,7 @@ static unsigned char *noalloc_scratch()
 extern "C" int zd_morton_sort_noalloc(const uint64_t *d_keys_in, int64_t n, int key_bits, uint64_t *d_keys_out,
                                       int32_t *d_perm_out, void *stream)
 {
+    zdk::NvtxScope nvtx_("zd_morton_sort_noalloc");
     using namespace zdk;
     if (n < 0 || key_bits < 1 || key_bits > 64) return ZD_ERR_INVALID_ARG;
     if (n > ZD_NOALLOC_MAX_KEYS) return ZD_ERR_CAPACITY;

@@ -14,12 +14,14 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libzd.so")
+# ZD_DEBUG=1 in the environment selects the debug build (index checks in the
+# kernels; see build_lib.py)
+LIB_PATH = os.path.join(_HERE, "_lib", "libzd_debug.so" if os.environ.get("ZD_DEBUG") == "1" else "libzd.so")
 
 ZD_OK = 0
 ZD_ERR_INVALID_ARG, ZD_ERR_RANGE, ZD_ERR_OOM, ZD_ERR_CUDA = 1, 2, 3, 4
 ZD_ERR_NOT_FOUND, ZD_ERR_DUPLICATE_ID, ZD_ERR_TIMEOUT = 5, 6, 7
-ZD_ERR_UNIMPLEMENTED, ZD_ERR_CAPACITY = 8, 9
+ZD_ERR_UNIMPLEMENTED, ZD_ERR_CAPACITY, ZD_ERR_INTERNAL = 8, 9, 10
 ZD_COORD_I32, ZD_COORD_F32 = 0, 1
 ZD_SEARCH_LEAF, ZD_SEARCH_BIT, ZD_SEARCH_ROOT = 0, 1, 2
 ZD_KNN_THREAD_PER_QUERY, ZD_KNN_WARP_GROUP = 0x100, 0x200

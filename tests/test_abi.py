@@ -48,8 +48,8 @@ def test_status_strings(lib):
     import ctypes
     _, so = lib
     so.zd_status_string.restype = ctypes.c_char_p
-    seen = {so.zd_status_string(i) for i in range(10)}
-    assert len(seen) == 10 and b"unknown status" not in seen
+    seen = {so.zd_status_string(i) for i in range(11)}
+    assert len(seen) == 11 and b"unknown status" not in seen
 
 
 def test_product_path_does_not_import_the_oracle():
@@ -119,3 +119,15 @@ def test_size_limits_rejected_on_the_host(lib):
                                    None) == zd.ZD_ERR_CAPACITY
     assert so.zd_knn_dist_backward(fake, fake, fake, 1 << 40, 1 << 40, 16, 3, 8, C.byref(one), 0, fake,
                                    fake, None) == zd.ZD_ERR_CAPACITY
+
+
+def test_debug_checks_compile(tmp_path):
+    """The -DZD_DEBUG variant of the kernels compiles (the debug library is
+    built on the GPU machine by build_lib.build(debug=True))."""
+    from paper_2111_04182_gb300 import build_lib
+    for src in ("sort.cu", "build.cu"):
+        cmd = [build_lib.nvcc()] + build_lib.ARCH + build_lib.FLAGS + ["-DZD_DEBUG", "-c",
+                                                                      os.path.join(build_lib.CSRC, src),
+                                                                      "-o", str(tmp_path / (src + ".o"))]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-3000:]
