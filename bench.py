@@ -107,21 +107,45 @@ WIDE_SOURCES = ["paper_2111_04182_gb300/csrc/knn_impl.cuh", "paper_2111_04182_gb
                 "paper_2111_04182_gb300/csrc/knn_wide.cu"]
 
 
-def profiled_traffic(kernel: str, workload: str, summary: str = "knn_allpoints_3d_clustered.md",
-                     sources=None):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
-    None when absent or when the kernel source changed since the capture."""
+def profiled_value(field: str, kernel: str, workload: str, summary: str, sources):
+    """A number `field` of `kernel` from a committed ncu summary line
+    `<field>: <value> source: <digest> kernel: <k> workload: <w>`, or None
+    when absent or when the kernel's sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+source:\s*([0-9a-f]+)\s+kernel:\s*(\S+)\s+workload:\s*(\S+)",
+    m = re.search(r"%s:\s*([0-9.]+)\s+source:\s*([0-9a-f]+)\s+kernel:\s*(\S+)\s+workload:\s*(\S+)" % field,
                   text)
     if not m or m.group(3) != kernel or m.group(4) != workload:
         return None
-    if m.group(2) != source_digest(sources or KNN_SOURCES):
+    if m.group(2) != source_digest(sources):
         return None
-    return int(m.group(1))
+    return float(m.group(1))
+
+
+def profiled_traffic(kernel: str, workload: str, summary: str = "knn_allpoints_3d_clustered.md",
+                     sources=None):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None when absent or when the kernel source changed since the capture."""
+    v = profiled_value("traffic_bytes_per_launch", kernel, workload, summary, sources or KNN_SOURCES)
+    return None if v is None else int(v)
+
+
+def issue_roofline(inst_per_unit, units: int, ms: float, sm_mhz) -> dict:
+    """Instruction-issue roofline: warp instructions per unit (from the
+    committed ncu summary) x units / the measured time, against the issue
+    peak of one warp instruction per cycle per scheduler (4 per SM)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = sms * 4 * (sm_mhz or 0) * 1e6
+    if inst_per_unit is None or not peak:
+        return {"bound": "issue", "achieved": None, "peak": peak or None, "unit": "warp-inst/s", "frac": None,
+                "inst_per_unit": inst_per_unit}
+    ach = inst_per_unit * units / (ms / 1e3)
+    return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp-inst/s", "frac": ach / peak,
+            "inst_per_unit": inst_per_unit, "peak_basis": "%d SMs x 4 schedulers x %.0f MHz (median under load)"
+            % (sms, sm_mhz)}
 
 
 class ClockSampler:
@@ -354,11 +378,13 @@ def run_ours(args):
     build_avg = sum(build_ms) / len(build_ms)
     achieved = kb / (knn_avg / 1e3) / 1e9
     traffic = profiled_traffic("k_knn_group", "3d-clustered-1e7") if n == 10_000_000 else None
+    ipq = (profiled_value("warp_inst_per_query", "k_knn_group", "3d-clustered-1e7",
+                          "knn_allpoints_3d_clustered.md", KNN_SOURCES) if n == 10_000_000 else None)
     bb = build_bytes_per_point() * n
     # build: liveness bitmap init, encode, plan, 8 sort passes, finish,
-    # gather, split flags, scan, leaf index, internal nodes, boxes, float
-    # copy (19); k-NN: warp groups + exact fallback (2)
-    launches_per_step = 21
+    # gather (+ float copy), split flags, scan, leaf index, internal nodes,
+    # boxes (18); k-NN: warp groups + exact fallback (2)
+    launches_per_step = 20
     out = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -370,6 +396,7 @@ def run_ours(args):
         "roofline": {"kernel": "k_knn_group<3,10,fs>", "bound": "hbm", "achieved": achieved, "peak": pk,
                      "peak_source": pk_src, "unit": "GB/s", "frac": achieved / pk,
                      "traffic": traffic, "algorithmic_bytes_per_launch": kb},
+        "issue_roofline": dict(issue_roofline(ipq, n, knn_avg, clk.get("sm_mhz")), kernel="k_knn_group<3,10,fs>"),
         "clocks": clk,
         "e2e": {"value": ws * n / (e2e_ms / 1e3), "unit": "queries/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": n * k * 12,

@@ -252,12 +252,13 @@ static int build_core(zd_tree *t, const void *d_pts, const int64_t *seg_off, int
     }
     {
         NvtxScope r("gather");
-        ZD_TRY(launch_gather(d_pts, dim, n, perm.p, t->keys, t->cloud_bit, t->cloud_off, 0, t->pts, s));
+        ZD_TRY(launch_gather(d_pts, dim, n, perm.p, t->keys, t->cloud_bit, t->cloud_off, 0, t->pts, s,
+                             t->is_float ? nullptr : t->fpts));
     }
     {
         NvtxScope r("topology");
         ZD_TRY(build_topology(t->keys, t->pts, n, t->p.leaf_size, dim, t->is_float, t->cloud_bit, topo_of(t),
-                              m));
+                              m, /*fpts_ready=*/true));
     }
     return m.failed ? ZD_ERR_OOM : ZD_OK;
 }

@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t *__restrict__ pts,
                                                 const int32_t *__restrict__ perm,
                                                 const u64 *__restrict__ keys, int cloud_bit,
                                                 const int64_t *__restrict__ cloud_off,
-                                                int32_t base_id, int4 *__restrict__ out, u32 *status)
+                                                int32_t base_id, int4 *__restrict__ out,
+                                                float4 *__restrict__ fout, u32 *status)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -38,21 +39,22 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t *__restrict__ pts,
         if (cloud_off) r.w = (int)(src - cloud_off[keys[i] >> cloud_bit]);
         else r.w = (int)(base_id + src);
         out[i] = r;
+        if (fout) fout[i] = make_float4((float)r.x, (float)r.y, (float)r.z, __int_as_float(r.w));
     }
 }
 
 int launch_gather(const void *pts_in, int dim, int64_t n, const int32_t *perm,
                   const u64 *sorted_keys, int cloud_bit, const int64_t *cloud_off, int32_t base_id,
-                  int4 *pts_out, cudaStream_t s)
+                  int4 *pts_out, cudaStream_t s, float4 *fpts_out)
 {
     if (n <= 0) return ZD_OK;
     unsigned g = grid_for(n, 256, 152 * 32);
     if (dim == 3)
         k_gather<3><<<g, 256, 0, s>>>((const int32_t *)pts_in, n, perm, sorted_keys, cloud_bit,
-                                      cloud_off, base_id, pts_out, status_word());
+                                      cloud_off, base_id, pts_out, fpts_out, status_word());
     else
         k_gather<2><<<g, 256, 0, s>>>((const int32_t *)pts_in, n, perm, sorted_keys, cloud_bit,
-                                      cloud_off, base_id, pts_out, status_word());
+                                      cloud_off, base_id, pts_out, fpts_out, status_word());
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }
@@ -460,7 +462,7 @@ int launch_group_starts(const int64_t *cloud_off, int64_t n_clouds, int64_t n_gr
 }
 
 int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, int dim,
-                   int is_float, int force_bit, const TopoBuffers &b, Mem &mem)
+                   int is_float, int force_bit, const TopoBuffers &b, Mem &mem, bool fpts_ready)
 {
     (void)dim;
     cudaStream_t s = mem.s;
@@ -502,7 +504,7 @@ int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, i
         k_boxes<false><<<grid_for(max_leaves, 256, 152 * 64), 256, 0, s>>>(
             pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter,
             b.fibox, b.flbox, status_word());
-    if (!is_float && b.fpts && n > 0)
+    if (!is_float && b.fpts && n > 0 && !fpts_ready)
         k_fpts<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(pts, n, b.fpts);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;

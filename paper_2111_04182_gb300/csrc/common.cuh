@@ -168,10 +168,11 @@ int radix_sort(const u64 *keys_in, int64_t n, int key_bits, u64 *keys_out, int32
 // ------------------------------------------------------------------ build
 // Gather sorted points: pts_out[i] = (coords of row perm[i], id), with
 // id = base_id + perm[i], or perm[i] - cloud_off[key >> cloud_bit] when
-// cloud_off is given.  Float points travel as their bit patterns.
+// cloud_off is given.  Float points travel as their bit patterns.  With
+// fpts_out (integer points), the exact float copy is written as well.
 int launch_gather(const void *pts_in, int dim, int64_t n, const int32_t *perm,
                   const u64 *sorted_keys, int cloud_bit, const int64_t *cloud_off, int32_t base_id,
-                  int4 *pts_out, cudaStream_t s);
+                  int4 *pts_out, cudaStream_t s, float4 *fpts_out = nullptr);
 
 struct TopoBuffers {
     int *leaf_of;
@@ -193,8 +194,9 @@ struct TopoBuffers {
 // Boundaries whose highest differing key bit is >= force_bit (the cloud id
 // bits of a forest; 64 for one tree) always separate leaves, so every
 // cloud's subtree is that cloud's own canonical tree.
+// fpts_ready: b.fpts was already written (by the gather).
 int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, int dim,
-                   int is_float, int force_bit, const TopoBuffers &b, Mem &mem);
+                   int is_float, int force_bit, const TopoBuffers &b, Mem &mem, bool fpts_ready = false);
 
 // Forests: group_start[g] = first sorted position of the g-th 32-point group,
 // groups laid out cloud by cloud so that none crosses a cloud boundary.
