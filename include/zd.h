@@ -25,7 +25,10 @@
  *   device-wide status word; zd_check() reads and clears it.
  * - The library owns the memory of a tree.  It allocates through the
  *   zd_allocator given to zd_build (stream-ordered); a NULL allocator means
- *   cudaMallocAsync / cudaFreeAsync on the call's stream.
+ *   the library's own stream-ordered pool on the current device
+ *   (cudaMallocFromPoolAsync / cudaFreeAsync on the call's stream), which
+ *   keeps up to ZD_POOL_KEEP_BYTES of freed memory reserved for reuse across
+ *   synchronizations instead of returning it to the driver at each one.
  * - Ids are int32.  zd_build gives point i the id i; inserts hand out new
  *   ids in order; deleted ids are never reused.
  * - A `const zd_tree*` may be searched from several streams at once (the
@@ -100,6 +103,10 @@ enum { ZD_KNN_ALL_POINTS = 0x400 };
  * carry a digit's running count in 30 bits.  Larger sizes return
  * ZD_ERR_CAPACITY before any work is enqueued. */
 #define ZD_MAX_KEYS 1073741823 /* 2^30 - 1 */
+
+/* Freed memory the default allocator's pool keeps reserved per device (8 GiB;
+ * beyond that it is returned to the driver at synchronization points). */
+#define ZD_POOL_KEEP_BYTES 8589934592ull
 
 typedef struct zd_params {
     int32_t dim;        /* 2 or 3 */

@@ -155,6 +155,7 @@ def zd_morton_sort(keys: torch.Tensor, key_bits: int = 64, stream=None):
 
 ZD_NOALLOC_MAX_KEYS = 1 << 20
 ZD_MAX_KEYS = (1 << 30) - 1
+ZD_POOL_KEEP_BYTES = 8 << 30
 
 
 def zd_morton_sort_noalloc(keys: torch.Tensor, key_bits: int = 64, stream=None, out=None):
