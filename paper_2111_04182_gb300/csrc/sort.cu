@@ -291,7 +291,7 @@ int launch_encode_f32(const float *pts, int64_t n, int dim, int coord_bits, cons
 
 // ------------------------------------------------------------ radix sort
 constexpr int SORT_THREADS = 256; // one thread per digit in the look-back
-constexpr int SORT_ITEMS = 16;
+constexpr int SORT_ITEMS = 12; // 3072-key tiles: 4 blocks per SM (measured: sort -6% vs 16 keys, 2 blocks)
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 // look-back word: 2 flag bits + a 30-bit count.  The count is a digit's
@@ -362,7 +362,7 @@ struct PassArgs {
     u32 *status;
 };
 
-__global__ void __launch_bounds__(SORT_THREADS) k_onesweep(PassArgs a, int pass)
+__global__ void __launch_bounds__(SORT_THREADS, 4) k_onesweep(PassArgs a, int pass)
 {
     const int q = a.plan->qidx[pass];
     if (q < 0) return; // every key has the same digit: nothing to do
