@@ -11,41 +11,12 @@
 #include <atomic>
 
 #include "common.cuh"
+#include "morton.cuh"
 
 namespace zdk {
 
 // ------------------------------------------------------------------ keys
-// Spread the low 21 bits of x so that bit b lands on bit 3b.
-__device__ __forceinline__ u64 spread3(u64 x)
-{
-    x &= 0x1fffffull;
-    x = (x | (x << 32)) & 0x001f00000000ffffull;
-    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
-    x = (x | (x << 8)) & 0x100f00f00f00f00full;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
-    return x;
-}
-
-// Spread the low 32 bits of x so that bit b lands on bit 2b.
-__device__ __forceinline__ u64 spread2(u64 x)
-{
-    x &= 0xffffffffull;
-    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
-    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
-    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
-    x = (x | (x << 2)) & 0x3333333333333333ull;
-    x = (x | (x << 1)) & 0x5555555555555555ull;
-    return x;
-}
-
-// Key bit d*b + (d-1-j) is bit b of coordinate j (x most significant).
-template <int DIM>
-__device__ __forceinline__ u64 interleave(u64 c0, u64 c1, u64 c2)
-{
-    if (DIM == 3) return (spread3(c0) << 2) | (spread3(c1) << 1) | spread3(c2);
-    return (spread2(c0) << 1) | spread2(c1);
-}
+// (the bit interleave itself is in morton.cuh)
 
 // Cloud (segment) of row i: the last c with seg_off[c] <= i.
 __device__ __forceinline__ int64_t segment_of(const int64_t *seg_off, int64_t n_seg, int64_t i)
