@@ -907,8 +907,10 @@ def bench_update_sweep(args):
     10^7 uniform points in [0, 2^20)^2, L = 16; for each batch size b an
     insert of b uniform points then a delete of those b ids (the set is
     restored each time), and bit-based queries in batches of m.
-    Insert and delete validate on the host (they sync), so their times are
-    whole-call latencies.  Queries use k = 1, 5 and 10.  At the end the tree
+    Batches above ZD_SMALL_BATCH validate on the host (they sync), so their
+    times are whole-call latencies; smaller ones run on the device without a
+    sync, and the re-derivation they leave for the next search is timed
+    separately.  Queries use k = 1, 5 and 10.  At the end the tree
     must equal a fresh build of the original points (same sorted keys and
     node structure)."""
     import torch
@@ -920,18 +922,49 @@ def bench_update_sweep(args):
     t = zd.zd_build(torch.from_numpy(pts).cuda(), 16, 20, capacity=n0 + max(sizes))
     ups = []
     for b in sizes:
-        ins_ms, del_ms = [], []
+        # small batches (no sync in the call) are timed as a run of R calls
+        # issued back to back, the way a stream of single updates runs; the
+        # latency of one isolated call (host enqueue included) is reported too
+        R = max(1, 64 // b) if b <= zd.ZD_SMALL_BATCH else 1
+        ins_ms, del_ms, one_ms = [], [], []
         for rep in range(args.warmup + max(1, args.steps // 3)):
-            batch = torch.from_numpy(datagen.uniform(rng, b, 2, 20)).cuda()
+            batches = [torch.from_numpy(datagen.uniform(rng, b, 2, 20)).cuda() for _ in range(R)]
             torch.cuda.synchronize()
-            e = _events(4)
-            e[0].record(); ids = t.insert(batch); e[1].record()
-            e[2].record(); t.delete(ids); e[3].record(); e[3].synchronize()
+            e = _events(6)
+            e[0].record(); ids = [t.insert(x) for x in batches]; e[1].record()
+            e[2].record()
+            for i in ids:
+                t.delete(i)
+            e[3].record(); e[3].synchronize()
+            one = datagen.uniform(rng, b, 2, 20)
+            onet = torch.from_numpy(one).cuda()
+            torch.cuda.synchronize()
+            e[4].record(); i1 = t.insert(onet); e[5].record(); e[5].synchronize()
+            t.delete(i1)
             if rep >= args.warmup:
-                ins_ms.append(e[0].elapsed_time(e[1])); del_ms.append(e[2].elapsed_time(e[3]))
-        im, dm = float(np.median(ins_ms)), float(np.median(del_ms))
-        ups.append({"batch": b, "insert_ms": im, "delete_ms": dm, "insert_s_per_point": im / 1e3 / b,
-                    "delete_s_per_point": dm / 1e3 / b})
+                ins_ms.append(e[0].elapsed_time(e[1]) / R); del_ms.append(e[2].elapsed_time(e[3]) / R)
+                one_ms.append(e[4].elapsed_time(e[5]))
+        im, dm, om = float(np.median(ins_ms)), float(np.median(del_ms)), float(np.median(one_ms))
+        ups.append({"batch": b, "calls_per_timing": R, "insert_ms": im, "delete_ms": dm,
+                    "insert_s_per_point": im / 1e3 / b, "delete_s_per_point": dm / 1e3 / b,
+                    "isolated_insert_call_ms": om})
+    # batches of at most ZD_SMALL_BATCH points are applied on the tree's pointer
+    # form; the next search re-derives the flat layout the searches read:
+    # time a one-query search right after a small insert + delete, beside the
+    # same search on a current tree
+    q1 = torch.from_numpy(datagen.uniform(rng, 1, 2, 20)).cuda()
+    first, steady = [], []
+    for rep in range(args.warmup + max(1, args.steps // 3)):
+        ids = t.insert(torch.from_numpy(datagen.uniform(rng, 1, 2, 20)).cuda())
+        t.delete(ids)
+        e = _events(4)
+        e[0].record(); t.knn(1, queries=q1, mode=zd.ZD_SEARCH_BIT); e[1].record()
+        e[2].record(); t.knn(1, queries=q1, mode=zd.ZD_SEARCH_BIT); e[3].record(); e[3].synchronize()
+        if rep >= args.warmup:
+            first.append(e[0].elapsed_time(e[1])); steady.append(e[2].elapsed_time(e[3]))
+    rederive = {"first_search_ms": float(np.median(first)), "search_ms": float(np.median(steady)),
+                "note": "first one-query search after a small insert + delete (re-derives the flat layout) "
+                        "vs the same search on a current tree"}
     qs = []
     for m in (1, 100, 10_000, 1_000_000, 10_000_000):
         q = torch.from_numpy(datagen.uniform(rng, m, 2, 20)).cuda()
@@ -954,7 +987,8 @@ def bench_update_sweep(args):
     big = ups[-1]
     return {"workload": "update-sweep-2d-%d" % n0, "metric": "updates/s and dynamic queries/s vs batch size",
             "value": big["batch"] / (big["insert_ms"] / 1e3), "unit": "updates/s (insert, largest batch)",
-            "updates": ups, "queries": qs, "tree_equals_fresh_build": same}
+            "updates": ups, "queries": qs, "rederive_after_small_batches": rederive,
+            "small_batch_limit": zd.ZD_SMALL_BATCH, "tree_equals_fresh_build": same}
 
 
 def bench_n_sweep(args):

@@ -249,18 +249,37 @@ int zd_export_tree(const zd_tree *t, int32_t *d_ids, uint64_t *d_keys, int32_t *
 int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k, int mode, int32_t *d_idx,
            void *d_dist, void *stream);
 
-/* Batch insert (Sec. 2 "Batch-dynamic updates", Algorithm 4): encode and sort
- * the batch, merge it into the sorted points and restructure the tree so that
- * it equals the canonical tree of the new point set.  d_pts [b, dim] in the
- * tree's coordinate type (integer trees only); d_new_ids [b] (may be NULL)
- * receives the ids given to the batch, in batch order.  Returns
- * ZD_ERR_CAPACITY if n + b exceeds the capacity.  Syncs `stream`. */
+/* Largest batch that zd_insert_batch / zd_delete_batch apply point by point
+ * on the device (below). */
+#define ZD_SMALL_BATCH 16
+
+/* Batch insert (Sec. 2 "Batch-dynamic updates", Algorithm 4): the tree
+ * afterwards equals the canonical tree of the new point set.  d_pts [b, dim]
+ * in the tree's coordinate type (integer trees only); d_new_ids [b] (may be
+ * NULL) receives the ids given to the batch, in batch order.  Returns
+ * ZD_ERR_CAPACITY if n + b exceeds the capacity.
+ * - b > ZD_SMALL_BATCH: encode and sort the batch, merge it into the sorted
+ *   points and re-derive the tree; validates by syncing `stream` before it
+ *   commits (a coordinate out of range returns ZD_ERR_RANGE, nothing changed).
+ * - b <= ZD_SMALL_BATCH: one device thread inserts the points one by one into
+ *   the tree's pointer form (descent by key bits, a new node where a key leaves
+ *   a node's prefix, a leaf split past L): O(depth) work per point and no
+ *   sync.  A coordinate out of range records ZD_ERR_RANGE for zd_check and the
+ *   batch changes nothing (its ids are used up).  The first such batch after a
+ *   build or a larger batch copies the tree into the pointer form and syncs
+ *   once; the next search, export, zd_tree_info_get or larger batch re-derives
+ *   the flat layout the searches read (O(n) work, syncs once).  Until then
+ *   the tree must not be searched from another stream. */
 int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t *d_new_ids, void *stream);
 
 /* Batch delete by id (Sec. 2: "deletions use an almost identical algorithm"):
  * the tree afterwards equals the canonical tree of the remaining points.
  * d_ids [b] must be distinct live ids; otherwise nothing is deleted and the
- * status is ZD_ERR_NOT_FOUND or ZD_ERR_DUPLICATE_ID.  Syncs `stream`. */
+ * status is ZD_ERR_NOT_FOUND or ZD_ERR_DUPLICATE_ID (returned for
+ * b > ZD_SMALL_BATCH, which syncs `stream`; recorded for zd_check for smaller
+ * batches, which do not sync and are applied point by point like small
+ * inserts: a leaf that empties is spliced out, a subtree that drops to L points
+ * becomes one leaf). */
 int zd_delete_batch(zd_tree *t, const int32_t *d_ids, int64_t b, void *stream);
 
 /* ------------------------------------------------------------- backward -- */

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["sort.cu", "build.cu", "knn_i32.cu", "knn_f32.cu", "knn_f32_2d.cu", "knn_f32_group.cu",
            "knn_f32_group_3n.cu", "knn_f32_group_3w.cu", "knn_f32_group_2n.cu", "knn_f32_group_2w.cu",
-           "knn_wide.cu", "update.cu", "backward.cu", "api.cu"]
+           "knn_wide.cu", "update.cu", "local.cu", "backward.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -127,7 +127,20 @@ struct zd_tree {
     int64_t n_groups;
     Block blocks[32];
     int nblocks;
+    // small update batches (local.cu): the pointer form, whether the flat
+    // arrays lag behind it, whether it lags behind the flat arrays, and the
+    // point updates it has taken since it was copied from them.  While the
+    // flat arrays lag, n is an upper bound (a rejected batch is not known
+    // until the flat arrays are re-derived).
+    LocalForm *local;
+    bool flat_stale, local_stale;
+    int64_t local_ops;
 };
+
+// The flat arrays that every search reads lag behind the pointer form after
+// small update batches; a search, export, info or large batch re-derives
+// them first (defined with the updates below).
+static int ensure_flat(zd_tree *t, cudaStream_t s);
 
 static Mem mem_of(const zd_tree *t, cudaStream_t s)
 {
@@ -153,6 +166,8 @@ static void tree_release(zd_tree *t, cudaStream_t s)
     Mem m = mem_of(t, s);
     for (int i = 0; i < t->nblocks; ++i) m.put(t->blocks[i].p, t->blocks[i].bytes);
     t->nblocks = 0;
+    local_release(t->local, m);
+    t->local = nullptr;
 }
 
 static TreeView view_of(const zd_tree *t)
@@ -252,6 +267,10 @@ static zd_tree *tree_new(const zd_params *p, const zd_allocator *alloc)
         t->has_alloc = true;
     }
     t->is_float = p->coord_type == ZD_COORD_F32;
+    t->local = nullptr;
+    t->flat_stale = false;
+    t->local_stale = true;
+    t->local_ops = 0;
     return t;
 }
 
@@ -499,6 +518,7 @@ int zd_free(zd_tree *t, void *stream)
 int zd_tree_info_get(const zd_tree *t, zd_tree_info *out, void *stream)
 {
     if (!t || !out) return ZD_ERR_INVALID_ARG;
+    ZD_TRY(ensure_flat(const_cast<zd_tree *>(t), (cudaStream_t)stream));
     int nl = 1;
     ZD_CUDA(cudaMemcpyAsync(&nl, t->meta, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     ZD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -558,6 +578,7 @@ extern "C" int zd_export_tree(const zd_tree *t, int32_t *d_ids, uint64_t *d_keys
                               int32_t *d_leaf_parent, void *d_node_box_lo, void *d_node_box_hi,
                               void *d_leaf_box_lo, void *d_leaf_box_hi, void *stream)
 {
+    if (t) ZD_TRY(ensure_flat(const_cast<zd_tree *>(t), (cudaStream_t)stream));
     NvtxScope nvtx_("zd_export_tree");
     if (!t) return ZD_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -694,6 +715,7 @@ extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k,
 {
     NvtxScope nvtx_("zd_knn");
     if (!t || !d_idx || k < 1) return ZD_ERR_INVALID_ARG;
+    ZD_TRY(ensure_flat(const_cast<zd_tree *>(t), (cudaStream_t)stream));
     if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
     if (t->cloud_off) return ZD_ERR_INVALID_ARG; // forests: zd_knn_batched
     cudaStream_t s = (cudaStream_t)stream;
@@ -754,61 +776,57 @@ int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *live
 int update_live_bits(u32 *live, int64_t a, int64_t z, int set, cudaStream_t s);
 } // namespace zdk
 
-extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t *d_new_ids, void *stream)
+// Grow the liveness bitmaps so that ids below `need` fit.
+static int grow_bits(zd_tree *t, int64_t need, Mem &mem)
 {
-    NvtxScope nvtx_("zd_insert_batch");
-    if (!t || b < 0 || (b > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
-    if (t->cloud_off || t->is_float) return ZD_ERR_UNIMPLEMENTED;
-    if (b == 0) return ZD_OK;
-    if (t->n + b > t->cap) return ZD_ERR_CAPACITY;
-    if (t->next_id + b >= ((int64_t)1 << 31) - 2) return ZD_ERR_CAPACITY;
-    cudaStream_t s = (cudaStream_t)stream;
+    if (need <= t->id_cap) return ZD_OK;
+    const int64_t nw = std::max<int64_t>(2 * t->id_words, (need + 31) / 32);
+    const size_t bytes = sizeof(u32) * (size_t)(2 * nw) + 16;
+    u32 *na = (u32 *)mem.get(bytes);
+    if (!na) return ZD_ERR_OOM;
+    k_grow_bits<<<grid_for(2 * nw, 256, 4096), 256, 0, mem.s>>>(t->alive, t->id_words, na, nw);
+    for (int i = 0; i < t->nblocks; ++i)
+        if (t->blocks[i].p == t->alive) {
+            mem.put(t->blocks[i].p, t->blocks[i].bytes);
+            t->blocks[i] = Block{na, bytes};
+        }
+    t->alive = na;
+    t->id_words = nw;
+    t->id_cap = 32 * nw;
+    return ZD_OK;
+}
+
+// Insert into the flat arrays (merge, then re-derive the tree), ids first_id..
+// Validates by syncing before it commits.
+static int flat_insert(zd_tree *t, const void *d_pts, int64_t b, int64_t first_id, int32_t *d_new_ids,
+                       cudaStream_t s)
+{
     Mem mem = mem_of(t, s);
-    // grow the liveness bitmaps if the new ids do not fit
-    if (t->next_id + b > t->id_cap) {
-        const int64_t nw = std::max<int64_t>(2 * t->id_words, (t->next_id + b + 31) / 32);
-        const size_t bytes = sizeof(u32) * (size_t)(2 * nw) + 16;
-        u32 *na = (u32 *)mem.get(bytes);
-        if (!na) return ZD_ERR_OOM;
-        k_grow_bits<<<grid_for(2 * nw, 256, 4096), 256, 0, s>>>(t->alive, t->id_words, na, nw);
-        for (int i = 0; i < t->nblocks; ++i)
-            if (t->blocks[i].p == t->alive) {
-                mem.put(t->blocks[i].p, t->blocks[i].bytes);
-                t->blocks[i] = Block{na, bytes};
-            }
-        t->alive = na;
-        t->id_words = nw;
-        t->id_cap = 32 * nw;
-    }
     // the previous call's device errors must not be mistaken for this one's
-    int prior = zd_check(stream);
+    int prior = zd_check(s);
     if (prior != ZD_OK) return prior;
     int r = update_insert(view_of(t), t->keys, t->pts, t->n, d_pts, b, t->p.dim, t->B, t->p.shift,
-                          t->key_bits, (int32_t)t->next_id, t->keys2, t->pts2, t->alive, d_new_ids, mem);
+                          t->key_bits, (int32_t)first_id, t->keys2, t->pts2, t->alive, d_new_ids, mem);
     if (r != ZD_OK) return r;
-    int st = zd_check(stream);
+    int st = zd_check(s);
     if (st != ZD_OK) {
         // nothing was committed: the new ids are released again
-        update_live_bits(t->alive, t->next_id, t->next_id + b, 0, s);
+        update_live_bits(t->alive, first_id, first_id + b, 0, s);
         return st;
     }
     std::swap(t->keys, t->keys2);
     std::swap(t->pts, t->pts2);
     t->n += b;
-    t->next_id += b;
     ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), mem));
     return mem.failed ? ZD_ERR_OOM : ZD_OK;
 }
 
-extern "C" int zd_delete_batch(zd_tree *t, const int32_t *d_ids, int64_t b, void *stream)
+// Delete from the flat arrays (compact, then re-derive the tree).  Validates
+// by syncing before it commits.
+static int flat_delete(zd_tree *t, const int32_t *d_ids, int64_t b, cudaStream_t s)
 {
-    NvtxScope nvtx_("zd_delete_batch");
-    if (!t || b < 0 || (b > 0 && !d_ids)) return ZD_ERR_INVALID_ARG;
-    if (t->cloud_off || t->is_float) return ZD_ERR_UNIMPLEMENTED;
-    if (b == 0) return ZD_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     Mem mem = mem_of(t, s);
-    int prior = zd_check(stream);
+    int prior = zd_check(s);
     if (prior != ZD_OK) return prior;
     int result = ZD_OK;
     u32 *live = t->alive, *marked = t->alive + t->id_words;
@@ -824,9 +842,111 @@ extern "C" int zd_delete_batch(zd_tree *t, const int32_t *d_ids, int64_t b, void
     std::swap(t->pts, t->pts2);
     t->n -= b;
     ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), mem));
-    int st = zd_check(stream);
+    int st = zd_check(s);
     if (st != ZD_OK) return st;
     return mem.failed ? ZD_ERR_OOM : ZD_OK;
+}
+
+// After small batches, re-derive the flat arrays from the pointer form
+// (syncs once); then replay, in order, the updates the pointer form could not
+// take (see local.cu).
+static int ensure_flat(zd_tree *t, cudaStream_t s)
+{
+    if (!t->flat_stale) return ZD_OK;
+    NvtxScope nvtx_("re-derive the flat tree");
+    Mem m = mem_of(t, s);
+    LocalLog log;
+    int64_t n = 0;
+    ZD_TRY(local_flatten(t->local, t->alive, t->next_id, t->key_bits, t->keys, t->pts, &n, &log, m));
+    t->n = n;
+    ZD_TRY(build_topology(t->keys, t->pts, n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), m));
+    t->flat_stale = false;
+    if (log.n == 0) return m.failed ? ZD_ERR_OOM : ZD_OK;
+    t->local_stale = true;
+    const int dim = t->p.dim;
+    for (int64_t i = 0; i < log.n;) {
+        int64_t j = i + 1;
+        if (log.op[i] == 1) { // a run of inserts with consecutive ids
+            while (j < log.n && log.op[j] == 1 && log.id[j] == log.id[i] + (j - i)) ++j;
+            std::vector<int32_t> h((size_t)(j - i) * dim);
+            for (int64_t e = i; e < j; ++e)
+                for (int c = 0; c < dim; ++c) h[(size_t)(e - i) * dim + c] = log.xyz[3 * e + c];
+            Scratch<int32_t> d(m, h.size());
+            if (!d.p) return ZD_ERR_OOM;
+            ZD_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, s));
+            ZD_TRY(flat_insert(t, d.p, j - i, log.id[i], nullptr, s)); // syncs: h outlives the copy
+        } else { // a run of deletes
+            while (j < log.n && log.op[j] != 1) ++j;
+            Scratch<int32_t> d(m, (size_t)(j - i));
+            if (!d.p) return ZD_ERR_OOM;
+            ZD_CUDA(cudaMemcpyAsync(d.p, log.id.data() + i, sizeof(int32_t) * (j - i), cudaMemcpyHostToDevice, s));
+            ZD_TRY(flat_delete(t, d.p, j - i, s));
+        }
+        i = j;
+    }
+    return m.failed ? ZD_ERR_OOM : ZD_OK;
+}
+
+// Before a small batch: a pointer form in step with the point set, with room
+// for b more point updates and ids.
+static int ensure_local(zd_tree *t, int64_t b, cudaStream_t s)
+{
+    if (t->local && !t->local_stale && t->local_ops + b <= LOCAL_BUDGET &&
+        t->next_id + b <= local_id_slots(t->local))
+        return ZD_OK;
+    ZD_TRY(ensure_flat(t, s));
+    Mem m = mem_of(t, s);
+    ZD_TRY(local_convert(&t->local, view_of(t), t->n, t->p.leaf_size, t->next_id + LOCAL_BUDGET, m));
+    t->local_stale = false;
+    t->local_ops = 0;
+    return m.failed ? ZD_ERR_OOM : ZD_OK;
+}
+
+extern "C" int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t *d_new_ids, void *stream)
+{
+    NvtxScope nvtx_("zd_insert_batch");
+    if (!t || b < 0 || (b > 0 && !d_pts)) return ZD_ERR_INVALID_ARG;
+    if (t->cloud_off || t->is_float) return ZD_ERR_UNIMPLEMENTED;
+    if (b == 0) return ZD_OK;
+    if (t->n + b > t->cap) return ZD_ERR_CAPACITY;
+    if (t->next_id + b >= ((int64_t)1 << 31) - 2) return ZD_ERR_CAPACITY;
+    cudaStream_t s = (cudaStream_t)stream;
+    Mem mem = mem_of(t, s);
+    ZD_TRY(grow_bits(t, t->next_id + b, mem));
+    if (b <= ZD_SMALL_BATCH) {
+        ZD_TRY(ensure_local(t, b, s));
+        ZD_TRY(local_insert(t->local, (const int32_t *)d_pts, b, t->p.dim, t->B, t->p.shift, (int32_t)t->next_id,
+                            d_new_ids, t->alive, s));
+        t->local_ops += b;
+        t->next_id += b;
+        t->n += b; // an upper bound until the flat arrays are re-derived
+        t->flat_stale = true;
+        return ZD_OK;
+    }
+    ZD_TRY(ensure_flat(t, s));
+    t->local_stale = true;
+    ZD_TRY(flat_insert(t, d_pts, b, t->next_id, d_new_ids, s));
+    t->next_id += b;
+    return ZD_OK;
+}
+
+extern "C" int zd_delete_batch(zd_tree *t, const int32_t *d_ids, int64_t b, void *stream)
+{
+    NvtxScope nvtx_("zd_delete_batch");
+    if (!t || b < 0 || (b > 0 && !d_ids)) return ZD_ERR_INVALID_ARG;
+    if (t->cloud_off || t->is_float) return ZD_ERR_UNIMPLEMENTED;
+    if (b == 0) return ZD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b <= ZD_SMALL_BATCH) {
+        ZD_TRY(ensure_local(t, b, s));
+        ZD_TRY(local_delete(t->local, d_ids, b, t->alive, t->id_cap, s));
+        t->local_ops += b;
+        t->flat_stale = true; // n stays an upper bound until then
+        return ZD_OK;
+    }
+    ZD_TRY(ensure_flat(t, s));
+    t->local_stale = true;
+    return flat_delete(t, d_ids, b, s);
 }
 
 extern "C" int zd_knn_dist_backward(const float *d_q, const float *d_ref, const int32_t *d_idx,

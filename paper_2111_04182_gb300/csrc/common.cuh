@@ -18,6 +18,8 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/zd.h"
 
 namespace zdk {
@@ -241,6 +243,36 @@ int launch_knn_group_f32(const KnnArgs &a, cudaStream_t s);
 // Large k (above the thread / group limits, up to ZD_MAX_K): one warp per
 // query, any mode, integer or float.
 int launch_knn_wide(const KnnArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------- small updates
+// (local.cu) The tree in pointer form, updated point by point by one device
+// thread without a host round trip; re-derived into the flat layout before
+// the next search.  The pools hold LOCAL_BUDGET point updates between two
+// copies from the flat tree; LOCAL_GROW_RESERVE slab entries serve leaves of
+// equal keys that outgrow their slab.
+constexpr int LOCAL_BUDGET = 1 << 16;
+constexpr int64_t LOCAL_GROW_RESERVE = 1 << 20;
+struct LocalForm;
+// Updates the pointer form could not apply (out of slab room), in order,
+// for replay through the flat update path.
+struct LocalLog {
+    int64_t n = 0;
+    std::vector<int> op, id, xyz; // op: 1 insert, 2 delete
+};
+// Copy the flat tree into a fresh pointer form for ids < id_slots (reads the
+// leaf count back: syncs once).
+int local_convert(LocalForm **lf, const TreeView &v, int64_t n, int L, int64_t id_slots, Mem &mem);
+int64_t local_id_slots(const LocalForm *lf);
+// One launch of one thread each; no sync.  Invalid batches record a status
+// and change nothing.
+int local_insert(LocalForm *lf, const int32_t *d_pts, int64_t b, int dim, int B, const uint32_t *shift,
+                 int32_t first_id, int32_t *d_new_ids, u32 *live, cudaStream_t s);
+int local_delete(LocalForm *lf, const int32_t *d_ids, int64_t b, u32 *live, int64_t id_cap, cudaStream_t s);
+// The pointer form's points in (key, id) order into keys_out / pts_out (syncs
+// to read the point count), and the log of updates it could not apply.
+int local_flatten(LocalForm *lf, const u32 *live, int64_t n_ids, int key_bits, u64 *keys_out, int4 *pts_out,
+                  int64_t *n_out, LocalLog *log, Mem &mem);
+void local_release(LocalForm *lf, Mem &mem);
 
 // --------------------------------------------------------------- backward
 int launch_backward(const float *q, const float *ref, const int32_t *idx, int64_t batch, int64_t m,

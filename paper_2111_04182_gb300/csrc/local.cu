@@ -1,0 +1,391 @@
+// local.cu -- small update batches on the pointer form of the tree
+// (local.cuh), and the way back to the flat layout the searches read.
+//
+// A tree starts flat (the build).  The first small batch copies the flat
+// tree into the pointer form (one thread per point, leaf and node; the leaf
+// count is read back once); from then on every small batch is one launch of
+// one thread that validates the batch on the device and applies it point by
+// point -- no host round trip.  The flat layout is re-derived from the
+// pointer form (points gathered in id order, stably sorted by key, topology
+// kernels of the build) before the next search, export or large batch.
+//
+// The pools are sized for LOCAL_BUDGET point updates; the host re-derives
+// and re-copies before that is exceeded.  Only a leaf of equal keys that
+// keeps growing can outrun the slab storage; then the batch kernel stops
+// applying, records the rest of the batch and every later small batch in a
+// log, and the host replays the log through the flat update path when it
+// re-derives the flat layout.
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "local.cuh"
+#include "morton.cuh"
+
+using namespace zdlocal;
+
+namespace zdk {
+
+constexpr int LOG_INSERT = 1, LOG_DELETE = 2;
+
+struct LocalForm {
+    LocalTree t;           // device pointers, counters at t.ctr
+    int64_t loc_cap;       // ids the location array covers
+    int log_cap;
+    int *log_op;           // [log_cap]
+    int *log_id;           // [log_cap]
+    int *log_xyz;          // [log_cap * 3]
+    std::vector<std::pair<void *, size_t>> blocks;
+};
+
+// ------------------------------------------------------------- flat -> pointer form
+__global__ void k_lf_entries(const u64 *__restrict__ keys, const int4 *__restrict__ pts,
+                             const int *__restrict__ leaf_of, const int *__restrict__ leaf_lo, int64_t n, int L,
+                             u64 *skeys, P4 *spts, LLoc *loc)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int j = leaf_of[p];
+        const int r = (int)(p - leaf_lo[j]);
+        // leaf j's slab holds its points with room for L + 1 more
+        const int64_t off = (int64_t)leaf_lo[j] + (int64_t)(L + 1) * j;
+        const int4 q = pts[p];
+        skeys[off + r] = keys[p];
+        spts[off + r] = P4{q.x, q.y, q.z, q.w};
+        loc[q.w] = LLoc{j, r};
+    }
+}
+
+__global__ void k_lf_leaves(const int *__restrict__ leaf_lo, const int *__restrict__ lparent,
+                            const int4 *__restrict__ lbox, const int *__restrict__ meta, int64_t max_leaves, int L,
+                            LLeaf *leaves)
+{
+    const int nl = meta[0];
+    for (int64_t jj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; jj < max_leaves;
+         jj += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)jj;
+        if (j >= nl) return;
+        LLeaf f;
+        f.parent = lparent[j];
+        f.size = leaf_lo[j + 1] - leaf_lo[j];
+        f.cap = f.size + L + 1;
+        f.pad = 0;
+        f.off = (int64_t)leaf_lo[j] + (int64_t)(L + 1) * j;
+        const int4 lo = lbox[2 * j], hi = lbox[2 * j + 1];
+        f.lo = P4{lo.x, lo.y, lo.z, 0};
+        f.hi = P4{hi.x, hi.y, hi.z, 0};
+        leaves[j] = f;
+    }
+}
+
+__global__ void k_lf_nodes(const u64 *__restrict__ keys, const int2 *__restrict__ ichild,
+                           const int *__restrict__ iparent, const int *__restrict__ ibit,
+                           const int2 *__restrict__ irange, const int4 *__restrict__ ibox,
+                           const int *__restrict__ meta, int64_t max_nodes, LNode *nodes)
+{
+    const int m = meta[0] - 1;
+    for (int64_t ii = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ii < max_nodes;
+         ii += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)ii;
+        if (i >= m) return;
+        LNode nd;
+        const int2 rg = irange[i], ch = ichild[i];
+        nd.key = keys[rg.x];
+        nd.left = ch.x;
+        nd.right = ch.y;
+        nd.parent = iparent[i];
+        nd.bit = ibit[i];
+        nd.size = rg.y - rg.x;
+        nd.pad = 0;
+        const int4 lo = ibox[2 * i], hi = ibox[2 * i + 1];
+        nd.lo = P4{lo.x, lo.y, lo.z, 0};
+        nd.hi = P4{hi.x, hi.y, hi.z, 0};
+        nodes[i] = nd;
+    }
+}
+
+__global__ void k_lf_counters(const int *meta, int64_t n, int L, LCounters *c)
+{
+    const int nl = n > 0 ? meta[0] : 0;
+    c->root = n == 0 ? LT_EMPTY : (nl > 1 ? 0 : ~0);
+    c->n_nodes = nl > 1 ? nl - 1 : 0;
+    c->n_leaves = nl;
+    c->count = (int)n;
+    c->stor_used = n + (int64_t)(L + 1) * nl;
+    c->state = 0;
+    c->log_n = 0;
+}
+
+// ------------------------------------------------------------- small batches
+__device__ void log_entry(LCounters *c, int log_cap, int *log_op, int *log_id, int *log_xyz, int op, int id,
+                          int x, int y, int z)
+{
+    const int e = c->log_n;
+    if (e >= log_cap) return; // the host bounds the logged updates by log_cap
+    log_op[e] = op;
+    log_id[e] = id;
+    log_xyz[3 * e] = x;
+    log_xyz[3 * e + 1] = y;
+    log_xyz[3 * e + 2] = z;
+    c->log_n = e + 1;
+}
+
+// One thread: insert b points (ids first_id + i).  The whole batch is
+// rejected (ZD_ERR_RANGE, nothing applied) if a coordinate is out of range.
+template <int DIM>
+__global__ void k_lf_insert(LocalTree t, const int32_t *__restrict__ pts, int64_t b, int B, uint3 shift,
+                            int32_t first_id, int32_t *new_ids, u32 *live, int log_cap, int *log_op, int *log_id,
+                            int *log_xyz, u32 *status)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int64_t lim = (int64_t)1 << B;
+    for (int64_t i = 0; i < b; ++i)
+        for (int j = 0; j < DIM; ++j) {
+            const int64_t c = (int64_t)pts[i * DIM + j] + (j == 0 ? shift.x : j == 1 ? shift.y : shift.z);
+            if (c < 0 || c >= lim) {
+                set_status(status, ZD_ERR_RANGE);
+                return;
+            }
+        }
+    if (new_ids)
+        for (int64_t i = 0; i < b; ++i) new_ids[i] = first_id + (int32_t)i;
+    LCounters *c = t.ctr;
+    for (int64_t i = 0; i < b; ++i) {
+        const int x = pts[i * DIM], y = pts[i * DIM + 1], z = DIM == 3 ? pts[i * DIM + 2] : 0;
+        const int id = first_id + (int)i;
+        if (c->state == 0) {
+            const u64 key = interleave<DIM>((u64)((int64_t)x + shift.x), (u64)((int64_t)y + shift.y),
+                                            (u64)((int64_t)z + (DIM == 3 ? shift.z : 0u)));
+            if (insert_point(t, key, P4{x, y, z, id}) == LT_OK) {
+                live[id >> 5] |= 1u << (id & 31);
+                continue;
+            }
+            c->state = 1; // out of slab room: this and later updates go to the log
+        }
+        log_entry(c, log_cap, log_op, log_id, log_xyz, LOG_INSERT, id, x, y, z);
+    }
+}
+
+// One thread: delete b ids.  The whole batch is rejected (nothing applied)
+// if an id is not live or repeats.  Once the form has fallen back, deletes
+// are logged unchecked and checked when the log is replayed.
+__global__ void k_lf_delete(LocalTree t, const int32_t *__restrict__ ids, int64_t b, u32 *live, int64_t id_cap,
+                            int log_cap, int *log_op, int *log_id, int *log_xyz, u32 *status)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    LCounters *c = t.ctr;
+    if (c->state == 0) {
+        for (int64_t i = 0; i < b; ++i) {
+            const int id = ids[i];
+            if (id < 0 || id >= id_cap || !((live[id >> 5] >> (id & 31)) & 1)) {
+                set_status(status, ZD_ERR_NOT_FOUND);
+                return;
+            }
+            for (int64_t k = 0; k < i; ++k)
+                if (ids[k] == id) {
+                    set_status(status, ZD_ERR_DUPLICATE_ID);
+                    return;
+                }
+        }
+    }
+    for (int64_t i = 0; i < b; ++i) {
+        const int id = ids[i];
+        if (c->state == 0) {
+            if (delete_point(t, id) == LT_OK) {
+                live[id >> 5] &= ~(1u << (id & 31));
+                continue;
+            }
+            c->state = 1;
+        }
+        log_entry(c, log_cap, log_op, log_id, log_xyz, LOG_DELETE, id, 0, 0, 0);
+    }
+}
+
+// ------------------------------------------------------------- pointer form -> flat
+// Points in id order: block_count[k] = live ids in [1024 k, 1024 k + 1024).
+__global__ void __launch_bounds__(1024) k_lf_count(const u32 *live, int64_t n_ids, int *block_count)
+{
+    const int64_t id = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    const bool on = id < n_ids && ((live[id >> 5] >> (id & 31)) & 1);
+    const int c = __syncthreads_count(on);
+    if (threadIdx.x == 0) block_count[blockIdx.x] = c;
+}
+
+// Exclusive scan of block_count in place (one block); total in block_count[nb].
+__global__ void __launch_bounds__(1024) k_lf_scan(int *block_count, int64_t nb)
+{
+    __shared__ int s_part[1024];
+    const int64_t per = (nb + 1023) / 1024;
+    const int64_t a = threadIdx.x * per, z = a + per < nb ? a + per : nb;
+    int sum = 0;
+    for (int64_t i = a; i < z; ++i) sum += block_count[i];
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const int v = s_part[i];
+            s_part[i] = run;
+            run += v;
+        }
+        block_count[nb] = run;
+    }
+    __syncthreads();
+    int run = s_part[threadIdx.x];
+    for (int64_t i = a; i < z; ++i) {
+        const int v = block_count[i];
+        block_count[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_lf_gather(LocalTree t, const u32 *live, int64_t n_ids,
+                                                    const int *block_off, u64 *keys_out, int4 *pts_out)
+{
+    __shared__ int s_warp[32];
+    const int64_t id = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    const bool on = id < n_ids && ((live[id >> 5] >> (id & 31)) & 1);
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    if (!on) return;
+    const int64_t pos = block_off[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u));
+    const LLoc l = t.loc[id];
+    const LLeaf &f = t.leaves[l.leaf];
+    keys_out[pos] = t.skeys[f.off + l.slot];
+    const P4 q = t.spts[f.off + l.slot];
+    pts_out[pos] = make_int4(q.x, q.y, q.z, q.w);
+}
+
+__global__ void k_lf_permute(const int4 *__restrict__ in, const int32_t *__restrict__ perm, int64_t n,
+                             int4 *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
+// ------------------------------------------------------------- host side
+template <typename T>
+static bool lf_alloc(LocalForm *lf, Mem &mem, T **p, size_t count)
+{
+    const size_t bytes = count * sizeof(T) + 16;
+    *p = (T *)mem.get(bytes);
+    if (!*p) return false;
+    lf->blocks.push_back({(void *)*p, bytes});
+    return true;
+}
+
+int64_t local_id_slots(const LocalForm *lf) { return lf ? lf->loc_cap : 0; }
+
+void local_release(LocalForm *lf, Mem &mem)
+{
+    if (!lf) return;
+    for (auto &b : lf->blocks) mem.put(b.first, b.second);
+    delete lf;
+}
+
+int local_convert(LocalForm **out, const TreeView &v, int64_t n, int L, int64_t id_slots, Mem &mem)
+{
+    cudaStream_t s = mem.s;
+    int nl = 0;
+    if (n > 0) {
+        ZD_CUDA(cudaMemcpyAsync(&nl, v.meta, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ZD_CUDA(cudaStreamSynchronize(s));
+    }
+    local_release(*out, mem);
+    *out = nullptr;
+    LocalForm *lf = new LocalForm();
+    LocalTree &t = lf->t;
+    t.L = L;
+    t.node_cap = nl + LOCAL_BUDGET + 1;
+    t.leaf_cap = nl + LOCAL_BUDGET + 1;
+    t.stor_cap = n + (int64_t)(L + 1) * nl + (int64_t)LOCAL_BUDGET * (3 * L + 3) + LOCAL_GROW_RESERVE;
+    lf->loc_cap = id_slots;
+    lf->log_cap = LOCAL_BUDGET;
+    bool ok = lf_alloc(lf, mem, &t.nodes, (size_t)t.node_cap) && lf_alloc(lf, mem, &t.leaves, (size_t)t.leaf_cap) &&
+              lf_alloc(lf, mem, &t.skeys, (size_t)t.stor_cap) && lf_alloc(lf, mem, &t.spts, (size_t)t.stor_cap) &&
+              lf_alloc(lf, mem, &t.loc, (size_t)id_slots) && lf_alloc(lf, mem, &t.ctr, 1) &&
+              lf_alloc(lf, mem, &lf->log_op, (size_t)lf->log_cap) &&
+              lf_alloc(lf, mem, &lf->log_id, (size_t)lf->log_cap) &&
+              lf_alloc(lf, mem, &lf->log_xyz, 3 * (size_t)lf->log_cap);
+    if (!ok) {
+        local_release(lf, mem);
+        return ZD_ERR_OOM;
+    }
+    if (n > 0) {
+        k_lf_entries<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(v.keys, v.pts, v.leaf_of, v.leaf_lo, n, L, t.skeys,
+                                                                t.spts, t.loc);
+        k_lf_leaves<<<grid_for(nl, 256, 152 * 32), 256, 0, s>>>(v.leaf_lo, v.lparent, v.lbox, v.meta, nl, L,
+                                                                t.leaves);
+        if (nl > 1)
+            k_lf_nodes<<<grid_for(nl - 1, 256, 152 * 32), 256, 0, s>>>(v.keys, v.ichild, v.iparent, v.ibit,
+                                                                       v.irange, v.ibox, v.meta, nl - 1, t.nodes);
+    }
+    k_lf_counters<<<1, 1, 0, s>>>(v.meta, n, L, t.ctr);
+    ZD_CUDA(cudaGetLastError());
+    *out = lf;
+    return ZD_OK;
+}
+
+int local_insert(LocalForm *lf, const int32_t *d_pts, int64_t b, int dim, int B, const uint32_t *shift,
+                 int32_t first_id, int32_t *d_new_ids, u32 *live, cudaStream_t s)
+{
+    const uint3 sh = make_uint3(shift ? shift[0] : 0, shift ? shift[1] : 0, shift ? shift[2] : 0);
+    if (dim == 3)
+        k_lf_insert<3><<<1, 1, 0, s>>>(lf->t, d_pts, b, B, sh, first_id, d_new_ids, live, lf->log_cap, lf->log_op,
+                                       lf->log_id, lf->log_xyz, status_word());
+    else
+        k_lf_insert<2><<<1, 1, 0, s>>>(lf->t, d_pts, b, B, sh, first_id, d_new_ids, live, lf->log_cap, lf->log_op,
+                                       lf->log_id, lf->log_xyz, status_word());
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+int local_delete(LocalForm *lf, const int32_t *d_ids, int64_t b, u32 *live, int64_t id_cap, cudaStream_t s)
+{
+    k_lf_delete<<<1, 1, 0, s>>>(lf->t, d_ids, b, live, id_cap, lf->log_cap, lf->log_op, lf->log_id, lf->log_xyz,
+                                status_word());
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+int local_flatten(LocalForm *lf, const u32 *live, int64_t n_ids, int key_bits, u64 *keys_out, int4 *pts_out,
+                  int64_t *n_out, LocalLog *log, Mem &mem)
+{
+    cudaStream_t s = mem.s;
+    LCounters c;
+    ZD_CUDA(cudaMemcpyAsync(&c, lf->t.ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
+    ZD_CUDA(cudaStreamSynchronize(s));
+    const int64_t n = c.count;
+    *n_out = n;
+    log->n = c.state ? c.log_n : 0;
+    if (log->n > 0) {
+        log->op.resize(log->n);
+        log->id.resize(log->n);
+        log->xyz.resize(3 * (size_t)log->n);
+        ZD_CUDA(cudaMemcpyAsync(log->op.data(), lf->log_op, sizeof(int) * log->n, cudaMemcpyDeviceToHost, s));
+        ZD_CUDA(cudaMemcpyAsync(log->id.data(), lf->log_id, sizeof(int) * log->n, cudaMemcpyDeviceToHost, s));
+        ZD_CUDA(cudaMemcpyAsync(log->xyz.data(), lf->log_xyz, 3 * sizeof(int) * log->n, cudaMemcpyDeviceToHost, s));
+        ZD_CUDA(cudaStreamSynchronize(s));
+    }
+    if (n == 0) return ZD_OK;
+    const int64_t nb = (n_ids + 1023) / 1024;
+    Scratch<int> boff(mem, (size_t)nb + 1);
+    Scratch<u64> k_id(mem, (size_t)n);
+    Scratch<int4> p_id(mem, (size_t)n);
+    Scratch<int32_t> perm(mem, (size_t)n);
+    if (!boff.p || !k_id.p || !p_id.p || !perm.p) return ZD_ERR_OOM;
+    k_lf_count<<<(unsigned)nb, 1024, 0, s>>>(live, n_ids, boff.p);
+    k_lf_scan<<<1, 1024, 0, s>>>(boff.p, nb);
+    k_lf_gather<<<(unsigned)nb, 1024, 0, s>>>(lf->t, live, n_ids, boff.p, k_id.p, p_id.p);
+    ZD_CUDA(cudaGetLastError());
+    // stable by key over points in id order: the (key, id) order
+    ZD_TRY(radix_sort(k_id.p, n, key_bits, keys_out, perm.p, nullptr, mem));
+    k_lf_permute<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(p_id.p, perm.p, n, pts_out);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+} // namespace zdk

@@ -156,6 +156,7 @@ def zd_morton_sort(keys: torch.Tensor, key_bits: int = 64, stream=None):
 ZD_NOALLOC_MAX_KEYS = 1 << 20
 ZD_MAX_KEYS = (1 << 30) - 1
 ZD_POOL_KEEP_BYTES = 8 << 30
+ZD_SMALL_BATCH = 16
 
 
 def zd_morton_sort_noalloc(keys: torch.Tensor, key_bits: int = 64, stream=None, out=None):
@@ -263,7 +264,9 @@ class ZdTree:
         return idx, dist
 
     def insert(self, pts: torch.Tensor, stream=None) -> torch.Tensor:
-        """Batch insert (Algorithm 4); returns the new ids.  Syncs."""
+        """Batch insert (Algorithm 4); returns the new ids.  Batches of at most
+        ZD_SMALL_BATCH points are applied on the device without a sync (a
+        range error goes to zd_check); larger ones sync and raise."""
         pts = _cuda(pts, torch.int32, "pts")
         ids = torch.empty(pts.shape[0], dtype=torch.int32, device=pts.device)
         _ok(_lib().zd_insert_batch(self.handle, _ptr(pts), pts.shape[0], _ptr(ids),
@@ -271,7 +274,9 @@ class ZdTree:
         return ids
 
     def delete(self, ids: torch.Tensor, stream=None) -> None:
-        """Batch delete by id.  Syncs."""
+        """Batch delete by id.  Batches of at most ZD_SMALL_BATCH ids are
+        applied on the device without a sync (unknown or repeated ids go to
+        zd_check); larger ones sync and raise."""
         ids = _cuda(ids, torch.int32, "ids")
         _ok(_lib().zd_delete_batch(self.handle, _ptr(ids), ids.numel(), C.c_void_p(_stream(stream))),
             "zd_delete_batch")

@@ -84,21 +84,27 @@ def test_insert_delete_rounds(zd, oracle):
 
 
 def test_update_errors_leave_tree_unchanged(zd, oracle):
+    """Invalid batches change nothing.  Batches of at most ZD_SMALL_BATCH
+    points record their error for zd_check (they do not sync); larger ones
+    validate on the host's side of a sync and return it."""
     rng = np.random.default_rng(5)
     pts = rng.integers(0, 2 ** 20, size=(5000, 3)).astype(np.int32)
     t = zd.zd_build(_t(pts), 8, 21, capacity=6000)
-    before = canonical(nodes_of(t.export()))
     for bad, code in (([1, 2, 99999], zd.ZD_ERR_NOT_FOUND), ([3, 4, 3], zd.ZD_ERR_DUPLICATE_ID),
                       ([-1], zd.ZD_ERR_NOT_FOUND)):
+        t.delete(_t(np.array(bad, np.int32)))
+        assert zd.zd_check() == code
+        big = np.concatenate([np.array(bad, np.int32), np.arange(100, 120, dtype=np.int32)])
         with pytest.raises(zd.ZdError) as e:
-            t.delete(_t(np.array(bad, np.int32)))
+            t.delete(_t(big))
         assert e.value.code == code
     t.delete(_t(np.array([10, 11], np.int32)))
+    t.delete(_t(np.array([10], np.int32)))  # already deleted
+    assert zd.zd_check() == zd.ZD_ERR_NOT_FOUND
+    t.insert(_t(np.array([[2 ** 21, 0, 0]], np.int32)))  # out of range
+    assert zd.zd_check() == zd.ZD_ERR_RANGE
     with pytest.raises(zd.ZdError) as e:
-        t.delete(_t(np.array([10], np.int32)))  # already deleted
-    assert e.value.code == zd.ZD_ERR_NOT_FOUND
-    with pytest.raises(zd.ZdError) as e:
-        t.insert(_t(np.array([[2 ** 21, 0, 0]], np.int32)))  # out of range
+        t.insert(_t(np.concatenate([np.zeros((20, 3), np.int32), np.array([[2 ** 21, 0, 0]], np.int32)])))
     assert e.value.code == zd.ZD_ERR_RANGE
     with pytest.raises(zd.ZdError) as e:
         t.insert(_t(rng.integers(0, 100, size=(2000, 3)).astype(np.int32)))
@@ -109,4 +115,3 @@ def test_update_errors_leave_tree_unchanged(zd, oracle):
     assert t.info()["n"] == 4998
     t.free()
     assert zd.zd_check() == 0
-    _ = before
