@@ -127,3 +127,31 @@ def test_equal_keys_past_the_slab_room_replay_exactly(zd, oracle):
     oset.delete(oset.ids[-2:])
     assert t.info()["n"] == len(oset.ids)
     t.free()
+
+
+def test_small_batches_on_an_empty_tree_with_a_shift(zd, oracle):
+    """A 2D tree with a coordinate shift, started empty, grown and emptied by
+    small batches only, up to exactly its capacity."""
+    rng = np.random.default_rng(17)
+    shift = [5, 1000]
+    t = zd.zd_build(_t(np.zeros((0, 2), np.int32)), 4, 12, shift=shift, capacity=40)
+    oset = oracle.OracleSet(np.zeros((0, 2), np.int32), 4, 12, shift=shift)
+    for _ in range(5):
+        ins = rng.integers(0, 2 ** 11, size=(8, 2)).astype(np.int32)
+        assert np.array_equal(t.insert(_t(ins)).cpu().numpy(), oset.insert(ins))
+        _same_tree(t, oset)
+    with pytest.raises(zd.ZdError) as e:  # 40 points: the capacity is full
+        t.insert(_t(np.zeros((1, 2), np.int32)))
+    assert e.value.code == zd.ZD_ERR_CAPACITY
+    while len(oset.ids):
+        dele = oset.ids[: zd.ZD_SMALL_BATCH].astype(np.int32)
+        t.delete(_t(dele))
+        oset.delete(dele)
+        assert zd.zd_check() == zd.ZD_OK
+        assert t.info()["n"] == len(oset.ids)
+        if len(oset.ids):
+            _same_tree(t, oset)
+    t.insert(_t(np.array([[1, 2]], np.int32)))
+    oset.insert(np.array([[1, 2]], np.int32))
+    _same_tree(t, oset)
+    t.free()
