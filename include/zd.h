@@ -267,9 +267,13 @@ int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k, int mode, 
  *   sync.  A coordinate out of range records ZD_ERR_RANGE for zd_check and the
  *   batch changes nothing (its ids are used up).  The first such batch after a
  *   build or a larger batch copies the tree into the pointer form and syncs
- *   once; the next search, export, zd_tree_info_get or larger batch re-derives
- *   the flat layout the searches read (O(n) work, syncs once).  Until then
- *   the tree must not be searched from another stream. */
+ *   once.  The searches read a flat layout of the tree: until it is
+ *   re-derived, external queries with k <= 32 that are fewer than a quarter
+ *   of the points search the pointer form directly (one thread per query,
+ *   the same exact answers); any other search, an export, zd_tree_info_get
+ *   or a larger batch re-derives the flat layout first (O(n) work, syncs
+ *   once).  While small batches are pending the tree must not be searched
+ *   from another stream. */
 int zd_insert_batch(zd_tree *t, const void *d_pts, int64_t b, int32_t *d_new_ids, void *stream);
 
 /* Batch delete by id (Sec. 2: "deletions use an almost identical algorithm"):

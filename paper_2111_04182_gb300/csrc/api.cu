@@ -715,7 +715,6 @@ extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k,
 {
     NvtxScope nvtx_("zd_knn");
     if (!t || !d_idx || k < 1) return ZD_ERR_INVALID_ARG;
-    ZD_TRY(ensure_flat(const_cast<zd_tree *>(t), (cudaStream_t)stream));
     if (k > ZD_MAX_K) return ZD_ERR_UNIMPLEMENTED;
     if (t->cloud_off) return ZD_ERR_INVALID_ARG; // forests: zd_knn_batched
     cudaStream_t s = (cudaStream_t)stream;
@@ -723,20 +722,28 @@ extern "C" int zd_knn(const zd_tree *t, const void *d_queries, int64_t m, int k,
     if (flags & ~(ZD_KNN_THREAD_PER_QUERY | ZD_KNN_WARP_GROUP)) return ZD_ERR_INVALID_ARG;
     const int base = mode & 0xff;
     if (base != ZD_SEARCH_LEAF && base != ZD_SEARCH_BIT && base != ZD_SEARCH_ROOT) return ZD_ERR_INVALID_ARG;
+    zd_tree *tw = const_cast<zd_tree *>(t); // its flat arrays are re-derived on demand
     if (base == ZD_SEARCH_LEAF || (mode & ZD_KNN_ALL_POINTS)) {
         if (d_queries) return ZD_ERR_INVALID_ARG;
+        ZD_TRY(ensure_flat(tw, s));
         return run_knn(t, nullptr, nullptr, t->n, k, base | flags, d_idx, d_dist, s);
     }
     mode = base;
     if (m < 0 || (m > 0 && !d_queries)) return ZD_ERR_INVALID_ARG;
     if (m > ZD_MAX_KEYS) return ZD_ERR_CAPACITY;
     if (m == 0) return ZD_OK;
+    // after small update batches, sparse queries search the pointer form (one
+    // thread per query, Algorithms 3 / 2) instead of re-deriving the flat
+    // arrays; dense ones re-derive them first and run the flat searches
+    const bool on_pointer_form = t->flat_stale && k <= LOCAL_MAX_K && 4 * m < t->n;
+    if (!on_pointer_form) ZD_TRY(ensure_flat(tw, s));
     Mem mem = mem_of(t, s);
     Scratch<u64> qkeys(mem, m);
     Scratch<int4> q4(mem, m);
     if (!qkeys.p || !q4.p) return ZD_ERR_OOM;
     ZD_TRY(prepare_queries(t, d_queries, m, nullptr, 1, mem, qkeys.p, q4.p));
-    ZD_TRY(run_knn(t, q4.p, qkeys.p, m, k, mode | flags, d_idx, d_dist, s));
+    if (on_pointer_form) ZD_TRY(local_knn(t->local, t->p.dim, q4.p, qkeys.p, m, k, mode, d_idx, d_dist, s));
+    else ZD_TRY(run_knn(t, q4.p, qkeys.p, m, k, mode | flags, d_idx, d_dist, s));
     return mem.failed ? ZD_ERR_OOM : ZD_OK;
 }
 

@@ -273,6 +273,12 @@ int local_delete(LocalForm *lf, const int32_t *d_ids, int64_t b, u32 *live, int6
 int local_flatten(LocalForm *lf, const u32 *live, int64_t n_ids, int key_bits, u64 *keys_out, int4 *pts_out,
                   int64_t *n_out, LocalLog *log, Mem &mem);
 void local_release(LocalForm *lf, Mem &mem);
+// External k-NN queries (already in Morton order, row in w) on the pointer
+// form, one thread per query, k <= LOCAL_MAX_K: what a search of a tree whose
+// flat arrays lag behind uses when its queries are sparse (no re-derivation).
+constexpr int LOCAL_MAX_K = 32;
+int local_knn(LocalForm *lf, int dim, const int4 *q4, const u64 *qkeys, int64_t m, int k, int mode,
+              int32_t *d_idx, void *d_dist, cudaStream_t s);
 
 // --------------------------------------------------------------- backward
 int launch_backward(const float *q, const float *ref, const int32_t *idx, int64_t batch, int64_t m,

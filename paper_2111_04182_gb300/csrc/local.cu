@@ -200,6 +200,189 @@ __global__ void k_lf_delete(LocalTree t, const int32_t *__restrict__ ids, int64_
     }
 }
 
+// ------------------------------------------------------------- searches
+// k-NN of external queries on the pointer form, one thread per query, exact
+// under the (squared distance, id) order: Algorithm 3 from the leaf the
+// query's key bits lead to (bit-based), or Algorithm 2 from the root
+// (root-based).  A node is visited iff its box distance^2 <= the current
+// K-th distance^2; the climb stops once no integer point outside the current
+// node's tight box can be within that distance (the node's points are the
+// only points inside its box: boxes lie in the nodes' Morton cells).
+template <int DIM>
+__device__ __forceinline__ long long lf_d2(int4 q, P4 p)
+{
+    const long long dx = (long long)q.x - p.x, dy = (long long)q.y - p.y;
+    long long s = dx * dx + dy * dy;
+    if (DIM == 3) {
+        const long long dz = (long long)q.z - p.z;
+        s += dz * dz;
+    }
+    return s;
+}
+
+template <int DIM>
+__device__ __forceinline__ long long lf_boxd2(int4 q, P4 lo, P4 hi)
+{
+    const long long cx = max(max((long long)lo.x - q.x, (long long)q.x - hi.x), 0ll);
+    const long long cy = max(max((long long)lo.y - q.y, (long long)q.y - hi.y), 0ll);
+    long long s = cx * cx + cy * cy;
+    if (DIM == 3) {
+        const long long cz = max(max((long long)lo.z - q.z, (long long)q.z - hi.z), 0ll);
+        s += cz * cz;
+    }
+    return s;
+}
+
+// every integer point outside [lo, hi] is farther than sqrt(r2) from q
+template <int DIM>
+__device__ __forceinline__ bool lf_inside(int4 q, P4 lo, P4 hi, long long r2)
+{
+    if (r2 == LLONG_MAX) return false;
+    const long long qq[3] = {q.x, q.y, q.z}, l[3] = {lo.x, lo.y, lo.z}, h[3] = {hi.x, hi.y, hi.z};
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        const long long m = min(qq[j] - l[j] + 1, h[j] + 1 - qq[j]);
+        if (m <= 0 || m * m <= r2) return false;
+    }
+    return true;
+}
+
+template <int DIM, int K>
+struct LfList {
+    long long d[K];
+    int id[K];
+    __device__ void init()
+    {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            d[j] = LLONG_MAX;
+            id[j] = -1;
+        }
+    }
+    __device__ __forceinline__ long long r2() const { return d[K - 1]; }
+    __device__ __forceinline__ void offer(long long dd, int ii)
+    {
+        if (!(dd < d[K - 1] || (dd == d[K - 1] && (unsigned)ii < (unsigned)id[K - 1]))) return;
+        bool placed = false;
+#pragma unroll
+        for (int j = K - 1; j > 0; --j) {
+            const bool lt = dd < d[j - 1] || (dd == d[j - 1] && (unsigned)ii < (unsigned)id[j - 1]);
+            if (!placed) {
+                d[j] = lt ? d[j - 1] : dd;
+                id[j] = lt ? id[j - 1] : ii;
+            }
+            placed = placed || !lt;
+        }
+        if (!placed) {
+            d[0] = dd;
+            id[0] = ii;
+        }
+    }
+};
+
+template <int DIM, int K>
+__device__ void lf_scan_leaf(const LocalTree &t, int j, int4 q, LfList<DIM, K> &L)
+{
+    const LLeaf &f = t.leaves[j];
+    for (int r = 0; r < f.size; ++r) {
+        const P4 p = t.spts[f.off + r];
+        L.offer(lf_d2<DIM>(q, p), p.w);
+    }
+}
+
+// Algorithm 2 from node v
+template <int DIM, int K>
+__device__ void lf_search_down(const LocalTree &t, int v, int4 q, LfList<DIM, K> &L, u32 *status)
+{
+    int stack[LT_MAX_DEPTH];
+    int sp = 0;
+    stack[sp++] = v;
+    while (sp) {
+        const int u = stack[--sp];
+        if (u < 0) {
+            const LLeaf &f = t.leaves[~u];
+            if (lf_boxd2<DIM>(q, f.lo, f.hi) <= L.r2()) lf_scan_leaf<DIM, K>(t, ~u, q, L);
+            continue;
+        }
+        const LNode &nd = t.nodes[u];
+        if (lf_boxd2<DIM>(q, nd.lo, nd.hi) > L.r2()) continue;
+        if (sp + 2 > LT_MAX_DEPTH) {
+            set_status(status, ZD_ERR_CUDA);
+            return;
+        }
+        stack[sp++] = nd.right; // the left child is searched first
+        stack[sp++] = nd.left;
+    }
+}
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(128) k_lf_knn(LocalTree t, const int4 *__restrict__ q4,
+                                                const u64 *__restrict__ qkeys, int64_t m, int k, int mode,
+                                                int32_t *out_idx, long long *out_d2, u32 *status)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int4 q = q4[i];
+        LfList<DIM, K> L;
+        L.init();
+        const int root = t.ctr->root;
+        if (root != LT_EMPTY) {
+            if (mode == ZD_SEARCH_ROOT || root < 0) {
+                lf_search_down<DIM, K>(t, root, q, L, status);
+            } else {
+                // bit-based start: follow the key bits down to a leaf
+                const u64 key = qkeys[i];
+                int v = root;
+                while (v >= 0) v = ((key >> t.nodes[v].bit) & 1) ? t.nodes[v].right : t.nodes[v].left;
+                lf_scan_leaf<DIM, K>(t, ~v, q, L);
+                // Algorithm 3: climb, searching each sibling, until the ball is inside
+                int node = v;
+                while (true) {
+                    const P4 lo = node < 0 ? t.leaves[~node].lo : t.nodes[node].lo;
+                    const P4 hi = node < 0 ? t.leaves[~node].hi : t.nodes[node].hi;
+                    if (lf_inside<DIM>(q, lo, hi, L.r2())) break;
+                    const int p = node < 0 ? t.leaves[~node].parent : t.nodes[node].parent;
+                    if (p < 0) break;
+                    const int sib = t.nodes[p].left == node ? t.nodes[p].right : t.nodes[p].left;
+                    lf_search_down<DIM, K>(t, sib, q, L, status);
+                    node = p;
+                }
+            }
+        }
+        int32_t *oi = out_idx + (int64_t)q.w * k;
+        long long *od = out_d2 ? out_d2 + (int64_t)q.w * k : nullptr;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (j < k) {
+                oi[j] = L.id[j];
+                if (od) od[j] = L.d[j];
+            }
+    }
+}
+
+template <int DIM>
+static void launch_lf_knn(const LocalTree &t, const int4 *q4, const u64 *qkeys, int64_t m, int k, int mode,
+                          int32_t *idx, long long *d2, cudaStream_t s)
+{
+    const unsigned g = grid_for(m, 128, 152 * 64);
+    u32 *st = status_word();
+    if (k <= 1) k_lf_knn<DIM, 1><<<g, 128, 0, s>>>(t, q4, qkeys, m, k, mode, idx, d2, st);
+    else if (k <= 2) k_lf_knn<DIM, 2><<<g, 128, 0, s>>>(t, q4, qkeys, m, k, mode, idx, d2, st);
+    else if (k <= 4) k_lf_knn<DIM, 4><<<g, 128, 0, s>>>(t, q4, qkeys, m, k, mode, idx, d2, st);
+    else if (k <= 8) k_lf_knn<DIM, 8><<<g, 128, 0, s>>>(t, q4, qkeys, m, k, mode, idx, d2, st);
+    else if (k <= 16) k_lf_knn<DIM, 16><<<g, 128, 0, s>>>(t, q4, qkeys, m, k, mode, idx, d2, st);
+    else k_lf_knn<DIM, 32><<<g, 128, 0, s>>>(t, q4, qkeys, m, k, mode, idx, d2, st);
+}
+
+int local_knn(LocalForm *lf, int dim, const int4 *q4, const u64 *qkeys, int64_t m, int k, int mode,
+              int32_t *d_idx, void *d_dist, cudaStream_t s)
+{
+    if (k > LOCAL_MAX_K) return ZD_ERR_INVALID_ARG;
+    if (dim == 3) launch_lf_knn<3>(lf->t, q4, qkeys, m, k, mode, d_idx, (long long *)d_dist, s);
+    else launch_lf_knn<2>(lf->t, q4, qkeys, m, k, mode, d_idx, (long long *)d_dist, s);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
 // ------------------------------------------------------------- pointer form -> flat
 // Points in id order: block_count[k] = live ids in [1024 k, 1024 k + 1024).
 __global__ void __launch_bounds__(1024) k_lf_count(const u32 *live, int64_t n_ids, int *block_count)

@@ -60,11 +60,20 @@ def test_small_batches_keep_the_canonical_tree(zd, oracle, dim, L, B):
                 t.delete(_t(dele))
                 oset.delete(dele)
         if step % 4 == 3 or step == 59:
+            # queries first: after small batches, sparse queries (300 here)
+            # search the pointer form; the export then re-derives the flat tree
+            kk = (1, 5, 12, 32)[(step // 4) % 4]
+            ot = oset.tree()
+            for mode, omode in ((zd.ZD_SEARCH_BIT, oracle.MODE_BIT), (zd.ZD_SEARCH_ROOT, oracle.MODE_ROOT)):
+                idx, d2 = t.knn(kk, queries=_t(q), mode=mode)
+                oi, od = ot.knn(kk, queries=q, mode=omode)
+                assert np.array_equal(idx.cpu().numpy(), oi), (step, mode)
+                assert np.array_equal(d2.cpu().numpy(), od), (step, mode)
             assert zd.zd_check() == zd.ZD_OK
             _same_tree(t, oset)
             assert t.info()["n"] == len(oset.ids)
-            idx, d2 = t.knn(5, queries=_t(q), mode=zd.ZD_SEARCH_BIT)
-            oi, od = oset.tree().knn(5, queries=q, mode=oracle.MODE_BIT)
+            idx, d2 = t.knn(5, queries=_t(q), mode=zd.ZD_SEARCH_BIT)  # the flat searches
+            oi, od = ot.knn(5, queries=q, mode=oracle.MODE_BIT)
             assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
     # all points, each excluding itself, rows by id
     idx, d2 = t.knn(4)
