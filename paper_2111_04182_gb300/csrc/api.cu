@@ -864,7 +864,7 @@ static int ensure_flat(zd_tree *t, cudaStream_t s)
     Mem m = mem_of(t, s);
     LocalLog log;
     int64_t n = 0;
-    ZD_TRY(local_flatten(t->local, t->alive, t->next_id, t->key_bits, t->keys, t->pts, &n, &log, m));
+    ZD_TRY(local_flatten(t->local, t->keys, t->pts, &n, &log, m));
     t->n = n;
     ZD_TRY(build_topology(t->keys, t->pts, n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), m));
     t->flat_stale = false;

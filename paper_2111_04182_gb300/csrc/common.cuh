@@ -270,8 +270,7 @@ int local_insert(LocalForm *lf, const int32_t *d_pts, int64_t b, int dim, int B,
 int local_delete(LocalForm *lf, const int32_t *d_ids, int64_t b, u32 *live, int64_t id_cap, cudaStream_t s);
 // The pointer form's points in (key, id) order into keys_out / pts_out (syncs
 // to read the point count), and the log of updates it could not apply.
-int local_flatten(LocalForm *lf, const u32 *live, int64_t n_ids, int key_bits, u64 *keys_out, int4 *pts_out,
-                  int64_t *n_out, LocalLog *log, Mem &mem);
+int local_flatten(LocalForm *lf, u64 *keys_out, int4 *pts_out, int64_t *n_out, LocalLog *log, Mem &mem);
 void local_release(LocalForm *lf, Mem &mem);
 // External k-NN queries (already in Morton order, row in w) on the pointer
 // form, one thread per query, k <= LOCAL_MAX_K: what a search of a tree whose

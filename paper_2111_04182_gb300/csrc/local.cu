@@ -6,8 +6,9 @@
 // count is read back once); from then on every small batch is one launch of
 // one thread that validates the batch on the device and applies it point by
 // point -- no host round trip.  The flat layout is re-derived from the
-// pointer form (points gathered in id order, stably sorted by key, topology
-// kernels of the build) before the next search, export or large batch.
+// pointer form (every leaf copies its sorted slab to its in-order position,
+// then the topology kernels of the build) before the next dense search,
+// export or large batch.
 //
 // The pools are sized for LOCAL_BUDGET point updates; the host re-derives
 // and re-copies before that is exceeded.  Only a leaf of equal keys that
@@ -384,69 +385,53 @@ int local_knn(LocalForm *lf, int dim, const int4 *q4, const u64 *qkeys, int64_t 
 }
 
 // ------------------------------------------------------------- pointer form -> flat
-// Points in id order: block_count[k] = live ids in [1024 k, 1024 k + 1024).
-__global__ void __launch_bounds__(1024) k_lf_count(const u32 *live, int64_t n_ids, int *block_count)
-{
-    const int64_t id = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-    const bool on = id < n_ids && ((live[id >> 5] >> (id & 31)) & 1);
-    const int c = __syncthreads_count(on);
-    if (threadIdx.x == 0) block_count[blockIdx.x] = c;
-}
+// The points in (key, id) order: one thread per leaf finds the leaf's first
+// sorted position (leaf_position) and copies its sorted slab into place.  A
+// slab longer than PLACE_THREAD entries (a leaf of equal keys) is cut into
+// chunks of PLACE_CHUNK entries that whole blocks copy in a second launch.
+constexpr int PLACE_THREAD = 64, PLACE_CHUNK = 2048;
 
-// Exclusive scan of block_count in place (one block); total in block_count[nb].
-__global__ void __launch_bounds__(1024) k_lf_scan(int *block_count, int64_t nb)
+struct PlaceChunk {
+    int leaf, start;
+    int64_t pos;
+};
+
+__global__ void k_lf_place(LocalTree t, int n_leaves, u64 *keys_out, int4 *pts_out, PlaceChunk *chunks,
+                           int *n_chunks)
 {
-    __shared__ int s_part[1024];
-    const int64_t per = (nb + 1023) / 1024;
-    const int64_t a = threadIdx.x * per, z = a + per < nb ? a + per : nb;
-    int sum = 0;
-    for (int64_t i = a; i < z; ++i) sum += block_count[i];
-    s_part[threadIdx.x] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int i = 0; i < 1024; ++i) {
-            const int v = s_part[i];
-            s_part[i] = run;
-            run += v;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_leaves; j += gridDim.x * blockDim.x) {
+        const LLeaf f = t.leaves[j];
+        if (f.size < 0) continue; // removed from the tree
+        const int64_t pos = leaf_position(t, j);
+        if (f.size > PLACE_THREAD) {
+            const int nc = (f.size + PLACE_CHUNK - 1) / PLACE_CHUNK;
+            const int c0 = atomicAdd(n_chunks, nc);
+            for (int c = 0; c < nc; ++c) chunks[c0 + c] = PlaceChunk{j, c * PLACE_CHUNK, pos + c * PLACE_CHUNK};
+            continue;
         }
-        block_count[nb] = run;
-    }
-    __syncthreads();
-    int run = s_part[threadIdx.x];
-    for (int64_t i = a; i < z; ++i) {
-        const int v = block_count[i];
-        block_count[i] = run;
-        run += v;
+        for (int r = 0; r < f.size; ++r) {
+            keys_out[pos + r] = t.skeys[f.off + r];
+            const P4 q = t.spts[f.off + r];
+            pts_out[pos + r] = make_int4(q.x, q.y, q.z, q.w);
+        }
     }
 }
 
-__global__ void __launch_bounds__(1024) k_lf_gather(LocalTree t, const u32 *live, int64_t n_ids,
-                                                    const int *block_off, u64 *keys_out, int4 *pts_out)
+__global__ void k_lf_place_chunks(LocalTree t, const PlaceChunk *__restrict__ chunks, const int *n_chunks,
+                                  u64 *keys_out, int4 *pts_out)
 {
-    __shared__ int s_warp[32];
-    const int64_t id = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-    const bool on = id < n_ids && ((live[id >> 5] >> (id & 31)) & 1);
-    const unsigned bal = __ballot_sync(0xffffffffu, on);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_warp[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += s_warp[w];
-    if (!on) return;
-    const int64_t pos = block_off[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u));
-    const LLoc l = t.loc[id];
-    const LLeaf &f = t.leaves[l.leaf];
-    keys_out[pos] = t.skeys[f.off + l.slot];
-    const P4 q = t.spts[f.off + l.slot];
-    pts_out[pos] = make_int4(q.x, q.y, q.z, q.w);
-}
-
-__global__ void k_lf_permute(const int4 *__restrict__ in, const int32_t *__restrict__ perm, int64_t n,
-                             int4 *__restrict__ out)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = in[perm[i]];
+    const int nc = *n_chunks;
+    for (int e = blockIdx.x; e < nc; e += gridDim.x) {
+        const PlaceChunk c = chunks[e];
+        const LLeaf f = t.leaves[c.leaf];
+        const int end = min(f.size - c.start, PLACE_CHUNK);
+        for (int r = threadIdx.x; r < end; r += blockDim.x) {
+            const int64_t src = f.off + c.start + r;
+            keys_out[c.pos + r] = t.skeys[src];
+            const P4 q = t.spts[src];
+            pts_out[c.pos + r] = make_int4(q.x, q.y, q.z, q.w);
+        }
+    }
 }
 
 // ------------------------------------------------------------- host side
@@ -534,8 +519,7 @@ int local_delete(LocalForm *lf, const int32_t *d_ids, int64_t b, u32 *live, int6
     return ZD_OK;
 }
 
-int local_flatten(LocalForm *lf, const u32 *live, int64_t n_ids, int key_bits, u64 *keys_out, int4 *pts_out,
-                  int64_t *n_out, LocalLog *log, Mem &mem)
+int local_flatten(LocalForm *lf, u64 *keys_out, int4 *pts_out, int64_t *n_out, LocalLog *log, Mem &mem)
 {
     cudaStream_t s = mem.s;
     LCounters c;
@@ -554,19 +538,16 @@ int local_flatten(LocalForm *lf, const u32 *live, int64_t n_ids, int key_bits, u
         ZD_CUDA(cudaStreamSynchronize(s));
     }
     if (n == 0) return ZD_OK;
-    const int64_t nb = (n_ids + 1023) / 1024;
-    Scratch<int> boff(mem, (size_t)nb + 1);
-    Scratch<u64> k_id(mem, (size_t)n);
-    Scratch<int4> p_id(mem, (size_t)n);
-    Scratch<int32_t> perm(mem, (size_t)n);
-    if (!boff.p || !k_id.p || !p_id.p || !perm.p) return ZD_ERR_OOM;
-    k_lf_count<<<(unsigned)nb, 1024, 0, s>>>(live, n_ids, boff.p);
-    k_lf_scan<<<1, 1024, 0, s>>>(boff.p, nb);
-    k_lf_gather<<<(unsigned)nb, 1024, 0, s>>>(lf->t, live, n_ids, boff.p, k_id.p, p_id.p);
+    // chunks: at most n / PLACE_CHUNK + (leaves longer than PLACE_THREAD)
+    const int64_t chunk_cap = n / PLACE_CHUNK + n / (PLACE_THREAD + 1) + 1;
+    Scratch<PlaceChunk> chunks(mem, chunk_cap);
+    Scratch<int> n_chunks(mem, 1);
+    if (!chunks.p || !n_chunks.p) return ZD_ERR_OOM;
+    ZD_CUDA(cudaMemsetAsync(n_chunks.p, 0, sizeof(int), s));
+    k_lf_place<<<grid_for(c.n_leaves, 256, 152 * 32), 256, 0, s>>>(lf->t, c.n_leaves, keys_out, pts_out, chunks.p,
+                                                                  n_chunks.p);
     ZD_CUDA(cudaGetLastError());
-    // stable by key over points in id order: the (key, id) order
-    ZD_TRY(radix_sort(k_id.p, n, key_bits, keys_out, perm.p, nullptr, mem));
-    k_lf_permute<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(p_id.p, perm.p, n, pts_out);
+    k_lf_place_chunks<<<152 * 4, 256, 0, s>>>(lf->t, chunks.p, n_chunks.p, keys_out, pts_out);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

@@ -61,7 +61,7 @@ struct LNode {
 
 struct LLeaf {
     int parent;
-    int size;
+    int size; // -1: a leaf that a splice or collapse removed from the tree
     int cap; // slab capacity
     int pad;
     int64_t off; // slab start in the entry storage
@@ -125,6 +125,22 @@ __host__ __device__ __forceinline__ int parent_of(const LocalTree &t, int ref)
 {
     return ref >= 0 ? t.nodes[ref].parent : t.leaves[~ref].parent;
 }
+// First sorted position of live leaf j: the leaves in key order are the
+// in-order leaves, so it is the number of points in the left subtrees that
+// the path from the leaf to the root passes on their right.
+__host__ __device__ __forceinline__ int64_t leaf_position(const LocalTree &t, int j)
+{
+    int64_t pos = 0;
+    int child = ~j;
+    int p = t.leaves[j].parent;
+    for (int d = 0; p >= 0 && d < LT_MAX_DEPTH; p = t.nodes[p].parent, ++d) {
+        const LNode &nd = t.nodes[p];
+        if (nd.right == child) pos += nd.left >= 0 ? t.nodes[nd.left].size : t.leaves[~nd.left].size;
+        child = p;
+    }
+    return pos;
+}
+
 __host__ __device__ __forceinline__ void set_parent(LocalTree &t, int ref, int p)
 {
     if (ref >= 0) t.nodes[ref].parent = p;
@@ -388,7 +404,7 @@ __host__ __device__ inline int collapse(LocalTree &t, int a)
             stack[sp++] = t.nodes[v].right; // left first out
             stack[sp++] = t.nodes[v].left;
         } else {
-            const LLeaf &src = t.leaves[~v];
+            LLeaf &src = t.leaves[~v];
             LLeaf &f = t.leaves[j];
             for (int r = 0; r < src.size; ++r) {
                 t.skeys[f.off + f.size] = t.skeys[src.off + r];
@@ -396,6 +412,7 @@ __host__ __device__ inline int collapse(LocalTree &t, int a)
                 t.loc[t.spts[f.off + f.size].w] = LLoc{j, f.size};
                 ++f.size;
             }
+            src.size = -1; // removed from the tree
         }
     }
     leaf_box(t, j);
@@ -435,6 +452,7 @@ __host__ __device__ inline int delete_point(LocalTree &t, int id)
     }
     // an empty leaf: its parent's other child takes the parent's place
     const int p = f.parent;
+    f.size = -1; // removed from the tree
     if (p < 0) {
         c.root = LT_EMPTY;
         return LT_OK;

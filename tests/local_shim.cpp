@@ -76,14 +76,18 @@ int lt_count(void *h) { return ((Shim *)h)->ctr.count; }
 
 // In-order walk: every node as (lo, hi, bit) over sorted positions (bit -1
 // for a leaf) with its box, and the points' ids and keys in sorted order.
-// Also checks the stored sizes and parents; returns the node count, or -1 if
-// a stored size or parent is inconsistent.
+// Also checks the stored sizes and parents and every leaf's computed first
+// position; returns the node count, or -1 if one of them is inconsistent.
 int64_t lt_export(void *h, int64_t *lo, int64_t *hi, int32_t *bit, int32_t *box_lo, int32_t *box_hi, int32_t *ids,
                   uint64_t *keys)
 {
     Shim *s = (Shim *)h;
     LocalTree &t = s->t;
-    if (s->ctr.root == LT_EMPTY) return 0;
+    if (s->ctr.root == LT_EMPTY) {
+        for (int j = 0; j < s->ctr.n_leaves; ++j)
+            if (t.leaves[j].size >= 0) return -1;
+        return 0;
+    }
     struct Frame {
         int ref, parent, state;
         int64_t lo, idx;
@@ -97,6 +101,7 @@ int64_t lt_export(void *h, int64_t *lo, int64_t *hi, int32_t *bit, int32_t *box_
         if (f.ref < 0) {
             const LLeaf &lf = t.leaves[~f.ref];
             if (lf.parent != f.parent) ok = false;
+            if (leaf_position(t, ~f.ref) != pos) ok = false; // the re-derivation's placement
             const int64_t a = pos;
             for (int r = 0; r < lf.size; ++r) {
                 ids[pos] = t.spts[lf.off + r].w;
@@ -139,6 +144,11 @@ int64_t lt_export(void *h, int64_t *lo, int64_t *hi, int32_t *bit, int32_t *box_
         }
     }
     if (pos != s->ctr.count) ok = false;
+    // the leaves not marked removed are exactly the reachable ones
+    int64_t reach = 0, marked_live = 0;
+    for (int64_t i = 0; i < nn; ++i) reach += bit[i] == -1;
+    for (int j = 0; j < s->ctr.n_leaves; ++j) marked_live += t.leaves[j].size >= 0;
+    if (reach != marked_live) ok = false;
     return ok ? nn : -1;
 }
 
