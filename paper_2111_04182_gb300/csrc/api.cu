@@ -213,6 +213,7 @@ static TopoBuffers topo_of(zd_tree *t)
     b.fpts = t->fpts;
     b.fibox = t->fibox;
     b.flbox = t->flbox;
+    b.fshift = make_uint3(t->p.shift[0], t->p.shift[1], t->p.shift[2]);
     return b;
 }
 
@@ -308,7 +309,7 @@ static int build_core(zd_tree *t, const void *d_pts, const int64_t *seg_off, int
     {
         NvtxScope r("gather");
         ZD_TRY(launch_gather(d_pts, dim, n, perm.p, t->keys, t->cloud_bit, t->cloud_off, 0, t->pts, s,
-                             t->is_float ? nullptr : t->fpts));
+                             t->is_float ? nullptr : t->fpts, topo_of(t).fshift));
     }
     {
         NvtxScope r("topology");

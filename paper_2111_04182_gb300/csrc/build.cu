@@ -19,6 +19,14 @@
 
 namespace zdk {
 
+// Exact float copy of an integer point: the shifted coordinates (c + shift
+// lies in [0, 2^B), B <= 24), id bits kept in w.
+__device__ __forceinline__ float4 shifted_float4(int4 p, uint3 sh)
+{
+    return make_float4((float)((unsigned)p.x + sh.x), (float)((unsigned)p.y + sh.y),
+                       (float)((unsigned)p.z + sh.z), __int_as_float(p.w));
+}
+
 // ----------------------------------------------------------------- gather
 template <int DIM>
 __global__ void __launch_bounds__(256) k_gather(const int32_t *__restrict__ pts, int64_t n,
@@ -26,7 +34,7 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t *__restrict__ pts,
                                                 const u64 *__restrict__ keys, int cloud_bit,
                                                 const int64_t *__restrict__ cloud_off,
                                                 int32_t base_id, int4 *__restrict__ out,
-                                                float4 *__restrict__ fout, u32 *status)
+                                                float4 *__restrict__ fout, uint3 fshift, u32 *status)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -39,22 +47,22 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t *__restrict__ pts,
         if (cloud_off) r.w = (int)(src - cloud_off[keys[i] >> cloud_bit]);
         else r.w = (int)(base_id + src);
         out[i] = r;
-        if (fout) fout[i] = make_float4((float)r.x, (float)r.y, (float)r.z, __int_as_float(r.w));
+        if (fout) fout[i] = shifted_float4(r, fshift);
     }
 }
 
 int launch_gather(const void *pts_in, int dim, int64_t n, const int32_t *perm,
                   const u64 *sorted_keys, int cloud_bit, const int64_t *cloud_off, int32_t base_id,
-                  int4 *pts_out, cudaStream_t s, float4 *fpts_out)
+                  int4 *pts_out, cudaStream_t s, float4 *fpts_out, uint3 fshift)
 {
     if (n <= 0) return ZD_OK;
     unsigned g = grid_for(n, 256, 152 * 32);
     if (dim == 3)
         k_gather<3><<<g, 256, 0, s>>>((const int32_t *)pts_in, n, perm, sorted_keys, cloud_bit,
-                                      cloud_off, base_id, pts_out, fpts_out, status_word());
+                                      cloud_off, base_id, pts_out, fpts_out, fshift, status_word());
     else
         k_gather<2><<<g, 256, 0, s>>>((const int32_t *)pts_in, n, perm, sorted_keys, cloud_bit,
-                                      cloud_off, base_id, pts_out, fpts_out, status_word());
+                                      cloud_off, base_id, pts_out, fpts_out, fshift, status_word());
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }
@@ -313,20 +321,18 @@ struct BoxOps<true> {
     }
 };
 
-__device__ __forceinline__ float4 as_float4(int4 v)
+__device__ __forceinline__ float4 as_float4(int4 v, uint3 sh)
 {
-    return make_float4((float)v.x, (float)v.y, (float)v.z, 0.f);
+    return shifted_float4(v, sh);
 }
 
-// Float copy of integer points (exact: coordinates lie in a window of width
-// <= 2^24), id bits kept in w.  The search filters candidates on it.
-__global__ void k_fpts(const int4 *__restrict__ pts, int64_t n, float4 *__restrict__ fpts)
+// Float copy of integer points (shifted_float4).  The search filters
+// candidates on it.
+__global__ void k_fpts(const int4 *__restrict__ pts, int64_t n, float4 *__restrict__ fpts, uint3 sh)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int4 p = pts[i];
-        fpts[i] = make_float4((float)p.x, (float)p.y, (float)p.z, __int_as_float(p.w));
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+        fpts[i] = shifted_float4(pts[i], sh);
 }
 
 // Atomic add with acquire-release semantics at device scope: it publishes
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
                                                const int *__restrict__ iparent,
                                                const int *__restrict__ lparent, int4 *ibox,
                                                int4 *lbox, int *counter, float4 *fibox, float4 *flbox,
-                                               u32 *status)
+                                               uint3 fshift, u32 *status)
 {
     typedef BoxOps<FLOAT> B;
     const int nl = meta[0];
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
         lbox[2 * j + 1] = hi;
         if (flbox) {
             // spare w lanes: the leaf's range of sorted positions
-            float4 flo = as_float4(lo), fhi = as_float4(hi);
+            float4 flo = as_float4(lo, fshift), fhi = as_float4(hi, fshift);
             flo.w = __int_as_float(leaf_lo[j]);
             fhi.w = __int_as_float(leaf_lo[j + 1]);
             flbox[2 * j] = flo;
@@ -386,7 +392,7 @@ __global__ void __launch_bounds__(256) k_boxes(const int4 *__restrict__ pts,
             ibox[2 * p + 1] = hi2;
             if (fibox) {
                 // spare w lanes: the two children
-                float4 flo = as_float4(lo2), fhi = as_float4(hi2);
+                float4 flo = as_float4(lo2, fshift), fhi = as_float4(hi2, fshift);
                 flo.w = __int_as_float(ch.x);
                 fhi.w = __int_as_float(ch.y);
                 fibox[2 * p] = flo;
@@ -499,13 +505,13 @@ int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, i
     if (is_float)
         k_boxes<true><<<grid_for(max_leaves, 256, 152 * 64), 256, 0, s>>>(
             pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter,
-            nullptr, nullptr, status_word());
+            nullptr, nullptr, make_uint3(0, 0, 0), status_word());
     else
         k_boxes<false><<<grid_for(max_leaves, 256, 152 * 64), 256, 0, s>>>(
             pts, b.leaf_lo, b.meta, max_leaves, b.ichild, b.iparent, b.lparent, b.ibox, b.lbox, b.counter,
-            b.fibox, b.flbox, status_word());
+            b.fibox, b.flbox, b.fshift, status_word());
     if (!is_float && b.fpts && n > 0 && !fpts_ready)
-        k_fpts<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(pts, n, b.fpts);
+        k_fpts<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(pts, n, b.fpts, b.fshift);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

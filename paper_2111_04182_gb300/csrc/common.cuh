@@ -171,10 +171,11 @@ int radix_sort(const u64 *keys_in, int64_t n, int key_bits, u64 *keys_out, int32
 // Gather sorted points: pts_out[i] = (coords of row perm[i], id), with
 // id = base_id + perm[i], or perm[i] - cloud_off[key >> cloud_bit] when
 // cloud_off is given.  Float points travel as their bit patterns.  With
-// fpts_out (integer points), the exact float copy is written as well.
+// fpts_out (integer points), the exact float copy of the coordinates plus
+// fshift is written as well.
 int launch_gather(const void *pts_in, int dim, int64_t n, const int32_t *perm,
                   const u64 *sorted_keys, int cloud_bit, const int64_t *cloud_off, int32_t base_id,
-                  int4 *pts_out, cudaStream_t s, float4 *fpts_out = nullptr);
+                  int4 *pts_out, cudaStream_t s, float4 *fpts_out = nullptr, uint3 fshift = {0, 0, 0});
 
 struct TopoBuffers {
     int *leaf_of;
@@ -188,8 +189,11 @@ struct TopoBuffers {
     int *lparent;
     int4 *lbox;
     int *counter; // scratch [n] for the bottom-up box pass
-    // integer trees whose coordinates fit fp32 exactly: float copies, or null
+    // integer trees with B <= 24: float copies of the SHIFTED coordinates
+    // (c + shift lies in [0, 2^B), so they are exact; differences of shifted
+    // coordinates are the coordinate differences), or null
     float4 *fpts, *fibox, *flbox;
+    uint3 fshift;
 };
 
 // From sorted keys and points, build leaves, internal nodes and boxes.

@@ -69,7 +69,7 @@ __device__ __forceinline__ void key_insert(u64 (&key)[K], u64 c)
 
 struct GroupCtx {
     int qx, qy, qz;
-    float fx, fy, fz;    // the same coordinates as exact floats
+    float fx, fy, fz;    // the shifted coordinates as exact floats
     int self;            // sorted position to skip (all-points), else -1
     bool live;           // the lane has a query
     int idb;             // id bits of the packed key
@@ -368,9 +368,10 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
     c.qx = qp.x;
     c.qy = qp.y;
     c.qz = qp.z;
-    c.fx = (float)qp.x;
-    c.fy = (float)qp.y;
-    c.fz = (float)qp.z;
+    // the float copies hold shifted coordinates (exact: c + shift < 2^24)
+    c.fx = (float)((unsigned)qp.x + a.shift.x);
+    c.fy = (float)((unsigned)qp.y + a.shift.y);
+    c.fz = (float)((unsigned)qp.z + a.shift.z);
     c.self = allpts && c.live ? qi : -1;
     c.idb = a.idb;
     c.sat = (1ull << (64 - a.idb)) - 1ull;

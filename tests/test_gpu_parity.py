@@ -279,6 +279,36 @@ def test_knn_external_queries(zd, oracle, mode, dim, mapping):
     t.free()
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_knn_far_from_the_origin(zd, oracle, dim, mapping):
+    """Coordinates near -2^29 and -2^30 brought into [0, 2^20) by a large
+    shift: the raw values are not exact in fp32, the shifted ones are.  The
+    all-points graph (clustered, with duplicates) and external queries
+    (bit- and root-based) must still equal the oracle's."""
+    rng = np.random.default_rng(40 + dim)
+    shift = [1 << 29, (1 << 30) + 12345, 7][:dim]
+    c = rng.integers(0, 2 ** 20, size=(10, dim))
+    u = np.clip(c[rng.integers(0, 10, 30_000)] + rng.normal(0, 300, (30_000, dim)), 0, 2 ** 20 - 1)
+    pts = (u.astype(np.int64) - np.array(shift, np.int64)).astype(np.int32)
+    pts[:200] = pts[200:400]  # duplicates
+    qu = rng.integers(0, 2 ** 20, size=(5_000, dim))
+    q = (qu - np.array(shift, np.int64)).astype(np.int32)
+    q[:40] = pts[:40]
+    t = zd.zd_build(_t(pts), 16, 20, shift=shift)
+    ot = oracle.OracleTree(pts, 16, 20, shift)
+    for k in (1, 10):
+        idx, d2 = t.knn(k, mapping=mapping)
+        oi, od = ot.knn(k)
+        assert np.array_equal(d2.cpu().numpy(), od) and np.array_equal(idx.cpu().numpy(), oi), k
+    for mode in (1, 2):
+        idx, d2 = t.knn(5, queries=_t(q), mode=mode, mapping=mapping)
+        oi, od = oracle.knn_brute(pts, 5, queries=q)
+        assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od), mode
+    assert zd.zd_check() == 0
+    t.free()
+
+
 def test_knn_2d_uniform_workload(zd, oracle):
     """The 2D workload at its full size: n = 100,000, L = 16, k = 10."""
     from paper_2111_04182_gb300 import datagen
