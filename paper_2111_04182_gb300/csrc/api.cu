@@ -31,6 +31,19 @@ u32 *status_word()
     return a;
 }
 
+int sm_count()
+{
+    static std::atomic<int> cnt[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    int v = cnt[dev].load(std::memory_order_acquire);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+        cnt[dev].store(v, std::memory_order_release);
+    }
+    return v;
+}
+
 // The default allocator's per-device memory pool.  The device's default
 // stream-ordered pool returns freed memory to the driver at every
 // synchronization (release threshold 0), so a caller that synchronizes between
@@ -701,10 +714,14 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
         a.n_groups = (m + 31) / 32;
     }
     // queries handed back to the exact one-thread kernel
-    Scratch<int> fix(mem, (size_t)(allpts ? t->n : m) + 1);
+    const int64_t nfix = allpts ? t->n : m;
+    const int nch = sm_count();
+    Scratch<int> fix(mem, (size_t)nfix + 1 + nch);
     if (!fix.p) return ZD_ERR_OOM;
     a.fix_count = fix.p;
     a.fix_list = fix.p + 1;
+    a.chunk_ctr = fix.p + 1 + nfix;
+    a.n_chunks = nch;
     if (t->is_float) return launch_knn_group_f32(a, s);
     // packed keys: the ids need idb bits
     a.idb = std::max(1, ceil_log2(t->cloud_off ? t->max_cloud : t->next_id));

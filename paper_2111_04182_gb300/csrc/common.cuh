@@ -47,6 +47,9 @@ __device__ __forceinline__ void set_status(u32 *status, int code)
 // Host: address of this device's status word (looked up once per device).
 u32 *status_word();
 
+// Host: this device's number of SMs (looked up once per device).
+int sm_count();
+
 // Debug builds (compiled with -DZD_DEBUG) check the index arithmetic of the
 // kernels before the accesses it guards: a failed check records
 // ZD_ERR_INTERNAL in the status word and evaluates to false, and the caller
@@ -236,6 +239,11 @@ struct KnnArgs {
     const int64_t *q_off;    // forests, external queries: device query offsets [n_clouds + 1]
     int *fix_list;           // queries whose packed k-th distance saturated
     int *fix_count;
+    // warp groups: one counter per chunk of the SM-affine group feed (zeroed
+    // by the launcher), n_chunks of them, or null for one group per warp
+    int *chunk_ctr;
+    int n_chunks;
+    int64_t chunk_len; // groups per chunk (the launcher sets it)
     // exact kernel restricted to listed sorted positions (fallback), or null
     const int *sel;
     const int *sel_count;

@@ -15,16 +15,18 @@
 // control flow is warp-uniform and every candidate point is loaded once per
 // warp (a broadcast) instead of once per lane.
 //
-// Each lane keeps its k best as 64-bit keys (d^2 << idb) | id, so the order of
-// keys is the order (d^2, id) and an insertion step is one 64-bit compare.
-// Candidates are first filtered on the plain d^2 against the lane's k-th d^2;
-// only survivors are packed.  d^2 saturates at sat = 2^(64-idb) - 1, and a
-// lane never searches beyond d^2 = sat - 1: its threshold starts there and
-// stays there while its k-th entry is missing or saturated, so a lane whose
-// neighbours lie that far (sparse outskirts of skewed data) does not drag
-// the whole group through the tree.  A query that ends with a missing or
-// saturated entry among its first k is handed to the exact
-// one-thread-per-query kernel.
+// The answer of a lane is its k best as 64-bit keys (d^2 << idb) | id, so the
+// order of keys is the order (d^2, id).  How a lane gets there depends on the
+// tree: with exact float copies of the coordinates (B <= 24) it ranks
+// candidates by fp32 estimates during the walk and ranks only the final band
+// exactly (BandLane, below); otherwise it inserts every candidate that beats
+// its k-th d^2 into the packed list (ExactLane).  d^2 saturates at
+// sat = 2^(64-idb) - 1, and a lane never searches beyond d^2 = sat - 1: its
+// threshold starts there and stays there while its k-th entry is missing or
+// saturated, so a lane whose neighbours lie that far (sparse outskirts of
+// skewed data) does not drag the whole group through the tree.  A query that
+// ends with a missing or saturated entry among its first k is handed to the
+// exact one-thread-per-query kernel.
 //
 // The climb stops on the node's Morton cell -- the box of all coordinates
 // whose keys share the node's prefix, which contains every point the node can
@@ -34,6 +36,9 @@
 // All-points queries lie in their own cells; external queries use the cell
 // only when their key carries the node's prefix, else the tight box.
 #pragma once
+
+#include <algorithm>
+#include <atomic>
 
 #include "knn_impl.cuh"
 
@@ -87,9 +92,9 @@ __device__ __forceinline__ long long thr_of(const u64 (&key)[K], const GroupCtx 
     return d >= c.sat ? (long long)(c.sat - 1) : (long long)d;
 }
 
-// Float filter threshold: every candidate with d^2 <= thr computes (three
-// roundings of nonnegative terms) a float d^2 <= thr * (1 + 2^-24)^3 <
-// thr_f, so the filter never drops a true candidate.
+// Float bound of an integer threshold: every candidate with d^2 <= thr has
+// a float estimate (three roundings of nonnegative terms) <= thr (1 + 2^-24)^3
+// < the returned value.
 __device__ __forceinline__ float thr_float(long long thr)
 {
     if (thr == LLONG_MAX) return __int_as_float(0x7f800000);
@@ -108,6 +113,15 @@ __device__ __forceinline__ float box_d2f(const GroupCtx &c, float4 lo, float4 hi
     return fmaf(cx, cx, cy * cy);
 }
 
+// Float estimate of a candidate's d^2 from the exact float copies: the
+// differences are exact, the sum rounds at most three times.
+template <int DIM>
+__device__ __forceinline__ float est_d2f(const GroupCtx &c, float4 p)
+{
+    const float x = c.fx - p.x, y = c.fy - p.y, z = DIM == 3 ? c.fz - p.z : 0.f;
+    return fmaf(x, x, fmaf(y, y, z * z));
+}
+
 template <int DIM>
 __device__ __forceinline__ long long box_d2(const GroupCtx &c, int4 lo, int4 hi)
 {
@@ -121,6 +135,18 @@ __device__ __forceinline__ long long box_d2(const GroupCtx &c, int4 lo, int4 hi)
     return s;
 }
 
+template <int DIM>
+__device__ __forceinline__ long long exact_d2i(const GroupCtx &c, int4 p)
+{
+    const int dx = c.qx - p.x, dy = c.qy - p.y;
+    long long d2 = (long long)dx * dx + (long long)dy * dy;
+    if (DIM == 3) {
+        const int dz = c.qz - p.z;
+        d2 += (long long)dz * dz;
+    }
+    return d2;
+}
+
 // Margin test on one axis: the first integer outside [lo, hi] is more than
 // sqrt(thr) away from q.
 __device__ __forceinline__ bool axis_inside(long long q, long long lo, long long hi, long long thr)
@@ -129,93 +155,231 @@ __device__ __forceinline__ bool axis_inside(long long q, long long lo, long long
     return m > 0 && m * m > thr;
 }
 
-// Scan sorted positions [a, b) for every lane.
-template <int DIM, int K>
-__device__ __forceinline__ void group_scan(const TreeView &t, int a, int b, const GroupCtx &c,
-                                           u64 (&key)[K], long long &thr)
-{
-    for (int p = a; p < b; ++p) {
-        const int4 pt = __ldg(t.pts + p);
-        const int dx = c.qx - pt.x, dy = c.qy - pt.y;
-        long long d2 = (long long)dx * dx + (long long)dy * dy;
-        if (DIM == 3) {
-            const int dz = c.qz - pt.z;
-            d2 += (long long)dz * dz;
+// What a lane learns from a node: whether it may hold a closer point, and
+// the node's sorted positions [a, b) (a leaf) or its children (a, b).
+struct Probe {
+    bool need;
+    int a, b;
+};
+
+// ------------------------------------------------------------------------
+// ExactLane: the k best as packed keys (d^2 << idb) | id, exact int64 d^2
+// for every candidate.  Trees whose coordinates do not fit fp32 (B > 24).
+template <int K>
+struct ExactLane {
+    u64 key[K];
+    long long thr; // the lane's search radius^2 (thr_of)
+
+    __device__ __forceinline__ void init(const GroupCtx &c, int *)
+    {
+#pragma unroll
+        for (int j = 0; j < K; ++j) key[j] = ~0ull;
+        thr = (long long)(c.sat - 1);
+    }
+    __device__ __forceinline__ long long climb_thr() const { return thr; }
+
+    template <int DIM>
+    __device__ __forceinline__ Probe probe(const TreeView &t, int v, const GroupCtx &c) const
+    {
+        int4 lo, hi;
+        node_box(t, v, lo, hi);
+        Probe r;
+        r.need = c.live && box_d2<DIM>(c, lo, hi) <= thr;
+        if (v < 0) {
+            r.a = __ldg(t.leaf_lo + ~v);
+            r.b = __ldg(t.leaf_lo + ~v + 1);
+        } else {
+            const int2 ch = __ldg(t.ichild + v);
+            r.a = ch.x;
+            r.b = ch.y;
         }
-        const bool pre = c.live && d2 <= thr && p != c.self;
-        if (__any_sync(0xffffffffu, pre)) {
-            if (pre) {
-                const u64 df = (u64)d2 < c.sat ? (u64)d2 : c.sat;
-                const u64 ck = (df << c.idb) | (u64)(unsigned)pt.w;
-                if (ck < key[K - 1]) {
-                    key_insert<K>(key, ck);
-                    thr = thr_of<K>(key, c);
+        return r;
+    }
+
+    template <int DIM>
+    __device__ __forceinline__ void scan(const TreeView &t, int a, int b, const GroupCtx &c)
+    {
+        for (int p = a; p < b; ++p) {
+            const int4 pt = __ldg(t.pts + p);
+            const long long d2 = exact_d2i<DIM>(c, pt);
+            const bool pre = c.live && d2 <= thr && p != c.self;
+            if (__any_sync(0xffffffffu, pre)) {
+                if (pre) {
+                    const u64 df = (u64)d2 < c.sat ? (u64)d2 : c.sat;
+                    const u64 ck = (df << c.idb) | (u64)(unsigned)pt.w;
+                    if (ck < key[K - 1]) {
+                        key_insert<K>(key, ck);
+                        thr = thr_of<K>(key, c);
+                    }
                 }
             }
         }
     }
-}
 
-// Exact test of one candidate that passed the float filter: the float
-// differences are exact integers, so the int64 d^2 is exact.
-template <int DIM, int K>
-__device__ __forceinline__ void accept_exact(int p, float dxf, float dyf, float dzf, int id,
-                                             const GroupCtx &c, u64 (&key)[K], long long &thr, float &thr_f)
-{
-    if (p == c.self) return;
-    const int dx = __float2int_rn(dxf), dy = __float2int_rn(dyf);
-    long long d2 = (long long)dx * dx + (long long)dy * dy;
-    if (DIM == 3) {
-        const int dz = __float2int_rn(dzf);
-        d2 += (long long)dz * dz;
+    template <int DIM>
+    __device__ __forceinline__ bool finish(const TreeView &, const GroupCtx &, u64 (&out)[K]) const
+    {
+#pragma unroll
+        for (int j = 0; j < K; ++j) out[j] = key[j];
+        return true;
     }
-    if (d2 > thr) return;
-    const u64 df = (u64)d2 < c.sat ? (u64)d2 : c.sat;
-    const u64 ck = (df << c.idb) | (u64)(unsigned)id;
-    if (ck < key[K - 1]) {
-        key_insert<K>(key, ck);
-        thr = thr_of<K>(key, c);
-        thr_f = thr_float(thr);
-    }
-}
+};
 
-// Scan sorted positions [a, b) on the float copy, two candidates per step.
-template <int DIM, int K>
-__device__ __forceinline__ void group_scan_f(const TreeView &t, int a, int b, const GroupCtx &c,
-                                             u64 (&key)[K], long long &thr, float &thr_f)
-{
-    int p = a;
-    for (; p + 1 < b; p += 2) {
-        const float4 u = __ldg(t.fpts + p), v = __ldg(t.fpts + p + 1);
-        const float ux = c.fx - u.x, uy = c.fy - u.y, uz = DIM == 3 ? c.fz - u.z : 0.f;
-        const float vx = c.fx - v.x, vy = c.fy - v.y, vz = DIM == 3 ? c.fz - v.z : 0.f;
-        const float du = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-        const float dv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-        const bool pu = c.live && du <= thr_f, pv = c.live && dv <= thr_f;
-        if (__any_sync(0xffffffffu, pu || pv)) {
-            if (pu) accept_exact<DIM, K>(p, ux, uy, uz, __float_as_int(u.w), c, key, thr, thr_f);
-            if (pv) accept_exact<DIM, K>(p + 1, vx, vy, vz, __float_as_int(v.w), c, key, thr, thr_f);
+// ------------------------------------------------------------------------
+// BandLane: trees with exact float copies (B <= 24).  The walk never touches
+// int64: a lane keeps only the K smallest fp32 estimates e[] it has seen (a
+// min/max network, no payload to move) and appends the sorted position of
+// every candidate it accepts to its column of the warp's shared buffer.
+//
+// Exactness.  With u = 2^-24, an estimate lies in [D (1-u)^3, D (1+u)^3] for
+// the exact d^2 = D (2D: squares of u).  K distinct candidates have estimate
+// <= eK = e[K-1], so the true K-th distance is <= eK / (1-u)^3 and every true
+// neighbour (ties by id included) has estimate <= eK (1+u)^3 / (1-u)^3 <
+// eK (1 + 2^-20) <= band.  Candidates are accepted while their estimate is
+// <= thr = eK (1 + 2^-19) rounded up; a box is pruned when its (exact-input)
+// estimate exceeds thr, which puts every point inside above
+// thr (1 - 6.1u) > band; the climb stops when every point outside the node
+// has D > ceil(thr), i.e. estimate > band.  eK only shrinks, so every true
+// neighbour is accepted when it is examined.  At the end the buffered
+// candidates whose estimate is <= band get their exact int64 d^2 and are
+// ranked by (d^2, id); the first k are the answer.
+//
+// thr never exceeds cap, the bound of d^2 = sat - 1 (a lane does not search
+// beyond the packed-key limit; see the saturation rule at the top).  A full
+// buffer is compacted, for every lane at once, to the entries still <= thr
+// (those above are no neighbours); a lane whose buffer stays full is handed
+// to the exact one-thread kernel.
+template <int K>
+struct BandCap { // buffered candidates per lane
+    static constexpr int value = K + 12 > 24 ? K + 12 : 24;
+};
+
+template <int K>
+struct BandLane {
+    static constexpr int CAP = BandCap<K>::value;
+    float e[K];  // the K smallest estimates, ascending
+    float thr;   // filter of candidates and boxes
+    float cap;   // thr <= cap
+    int cnt;     // buffered candidates
+    bool over;   // the buffer overflowed: exact fallback
+    int *buf;    // this lane's column: entry s at buf[32 s]
+
+    __device__ __forceinline__ void init(const GroupCtx &c, int *col)
+    {
+#pragma unroll
+        for (int j = 0; j < K; ++j) e[j] = __int_as_float(0x7f800000);
+        cap = thr_float((long long)(c.sat - 1));
+        thr = cap;
+        cnt = 0;
+        over = false;
+        buf = col;
+    }
+    __device__ __forceinline__ long long climb_thr() const { return __float2ll_ru(thr); }
+
+    template <int DIM>
+    __device__ __forceinline__ Probe probe(const TreeView &t, int v, const GroupCtx &c) const
+    {
+        // the float boxes carry the leaf range / the children in w
+        const float4 *fb = v < 0 ? t.flbox + 2 * (~v) : t.fibox + 2 * v;
+        const float4 lo = __ldg(fb), hi = __ldg(fb + 1);
+        Probe r;
+        r.need = c.live && box_d2f<DIM>(c, lo, hi) <= thr;
+        r.a = __float_as_int(lo.w);
+        r.b = __float_as_int(hi.w);
+        return r;
+    }
+
+    __device__ __forceinline__ void take(float est, int p)
+    {
+        if (!over) {
+            if (cnt < CAP) buf[32 * cnt++] = p;
+            else over = true;
+        }
+#pragma unroll
+        for (int j = K - 1; j > 0; --j) e[j] = fmaxf(e[j - 1], fminf(e[j], est));
+        e[0] = fminf(e[0], est);
+        thr = fminf(__fmul_ru(e[K - 1], 1.0f + 1.0f / 524288.0f), cap);
+    }
+
+    // Warp-uniform: when some lane has fewer than two free entries, every
+    // lane drops its entries above thr.
+    template <int DIM>
+    __device__ __forceinline__ void settle(const TreeView &t, const GroupCtx &c)
+    {
+        if (!__any_sync(0xffffffffu, !over && cnt > CAP - 2)) return;
+        if (over) return;
+        int w = 0;
+        for (int s = 0; s < cnt; ++s) {
+            const int p = buf[32 * s];
+            if (est_d2f<DIM>(c, __ldg(t.fpts + p)) <= thr) buf[32 * w++] = p;
+        }
+        cnt = w;
+        over = cnt > CAP - 2; // the band alone fills it
+    }
+
+    // Sorted positions [a, b) for every lane, two candidates per step.
+    template <int DIM>
+    __device__ __forceinline__ void scan(const TreeView &t, int a, int b, const GroupCtx &c)
+    {
+        int p = a;
+        for (; p + 1 < b; p += 2) {
+            const float4 u = __ldg(t.fpts + p), v = __ldg(t.fpts + p + 1);
+            const float eu = est_d2f<DIM>(c, u), ev = est_d2f<DIM>(c, v);
+            const bool pu = c.live && eu <= thr && p != c.self;
+            const bool pv = c.live && ev <= thr && p + 1 != c.self;
+            if (__any_sync(0xffffffffu, pu || pv)) {
+                if (pu) take(eu, p);
+                if (pv && ev <= thr) take(ev, p + 1);
+                settle<DIM>(t, c);
+            }
+        }
+        if (p < b) {
+            const float eu = est_d2f<DIM>(c, __ldg(t.fpts + p));
+            const bool pu = c.live && eu <= thr && p != c.self;
+            if (__any_sync(0xffffffffu, pu)) {
+                if (pu) take(eu, p);
+                settle<DIM>(t, c);
+            }
         }
     }
-    if (p < b) {
-        const float4 u = __ldg(t.fpts + p);
-        const float ux = c.fx - u.x, uy = c.fy - u.y, uz = DIM == 3 ? c.fz - u.z : 0.f;
-        const float du = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-        const bool pu = c.live && du <= thr_f;
-        if (__any_sync(0xffffffffu, pu)) {
-            if (pu) accept_exact<DIM, K>(p, ux, uy, uz, __float_as_int(u.w), c, key, thr, thr_f);
+
+    // The exact ranking of the band; false if the buffer overflowed.
+    template <int DIM>
+    __device__ __forceinline__ bool finish(const TreeView &t, const GroupCtx &c, u64 (&out)[K]) const
+    {
+#pragma unroll
+        for (int j = 0; j < K; ++j) out[j] = ~0ull;
+        if (over) return false;
+        const float band = __fmul_ru(e[K - 1], 1.0f + 1.0f / 1048576.0f);
+        for (int s = 0; s < cnt; ++s) {
+            const int p = buf[32 * s];
+            if (est_d2f<DIM>(c, __ldg(t.fpts + p)) > band) continue;
+            const int4 pt = __ldg(t.pts + p);
+            const long long d2 = exact_d2i<DIM>(c, pt);
+            const u64 df = (u64)d2 < c.sat ? (u64)d2 : c.sat;
+            const u64 ck = (df << c.idb) | (u64)(unsigned)pt.w;
+            if (ck < out[K - 1]) key_insert<K>(out, ck);
         }
+        return true;
     }
-}
+};
+
+template <int K, bool BAND>
+struct LaneOf {
+    typedef ExactLane<K> type;
+};
+template <int K>
+struct LaneOf<K, true> {
+    typedef BandLane<K> type;
+};
 
 // searchDown (Algorithm 2) for the whole group from `start`, skipping the
 // leaves l0..l1 scanned already; the stack lives in shared memory and every
 // lane holds the same stack pointer.  Children are pushed in the order of the
 // group's middle key (the side of the split it lies on goes first).
-template <int DIM, int K, bool FS>
+template <int DIM, class Lane>
 __device__ __forceinline__ void group_search(const TreeView &t, int start, int l0, int l1, u64 mid_key,
-                                             int *stack, const GroupCtx &c, u64 (&key)[K], long long &thr,
-                                             float &thr_f, u32 *status)
+                                             int *stack, const GroupCtx &c, Lane &L, u32 *status)
 {
     const int lane = threadIdx.x & 31;
     int sp = 0;
@@ -225,37 +389,20 @@ __device__ __forceinline__ void group_search(const TreeView &t, int start, int l
         // the nearer child is searched next directly; the farther one waits
         // on the stack (lane 0 writes it, every lane holds the same pointer)
         if (!(v < 0 && ~v >= l0 && ~v <= l1)) { // else scanned already
-            bool need;
-            float4 flo, fhi;
-            if (FS) {
-                const float4 *fb = v < 0 ? t.flbox + 2 * (~v) : t.fibox + 2 * v;
-                flo = __ldg(fb);
-                fhi = __ldg(fb + 1);
-                need = c.live && box_d2f<DIM>(c, flo, fhi) <= thr_f;
-            } else {
-                int4 lo, hi;
-                node_box(t, v, lo, hi);
-                need = c.live && box_d2<DIM>(c, lo, hi) <= thr;
-            }
-            if (__any_sync(0xffffffffu, need)) {
+            const Probe pr = L.template probe<DIM>(t, v, c);
+            if (__any_sync(0xffffffffu, pr.need)) {
                 if (v < 0) {
-                    if (FS) {
-                        group_scan_f<DIM, K>(t, __float_as_int(flo.w), __float_as_int(fhi.w), c, key, thr, thr_f);
-                    } else {
-                        const int a = __ldg(t.leaf_lo + ~v), b = __ldg(t.leaf_lo + ~v + 1);
-                        group_scan<DIM, K>(t, a, b, c, key, thr);
-                    }
+                    L.template scan<DIM>(t, pr.a, pr.b, c);
                 } else {
-                    const int2 ch = FS ? make_int2(__float_as_int(flo.w), __float_as_int(fhi.w)) : __ldg(t.ichild + v);
                     const bool right_first = (mid_key >> __ldg(t.ibit + v)) & 1;
                     if (sp + 1 > GROUP_STACK) {
                         if (lane == 0) set_status(status, ZD_ERR_CUDA);
                         return;
                     }
-                    if (lane == 0) stack[sp] = right_first ? ch.x : ch.y; // the far child waits
+                    if (lane == 0) stack[sp] = right_first ? pr.a : pr.b; // the far child waits
                     ++sp;
                     __syncwarp();
-                    v = right_first ? ch.y : ch.x;
+                    v = right_first ? pr.b : pr.a;
                     continue;
                 }
             }
@@ -278,10 +425,9 @@ __device__ __forceinline__ int descend_by_bits(const TreeView &t, int root, u64 
 }
 
 // Steps 1-3 of the group search (see the top of this file).
-template <int DIM, int K, bool FS>
-__device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs &a, const GroupCtx &c,
-                                               u64 (&key)[K], long long &thr, float &thr_f, int g0, int gend,
-                                               bool allpts, int *stack, u32 *status)
+template <int DIM, class Lane>
+__device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs &a, const GroupCtx &c, Lane &L,
+                                               int g0, int gend, bool allpts, int *stack, u32 *status)
 {
     // 1. the start leaves: consecutive in leaf order, since queries are sorted
     int l0, l1;
@@ -303,14 +449,13 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
     }
     if (!ZD_DCHECK(l0 >= 0 && l0 <= l1 && node_in_range(t, ~l1), status)) return;
     const int P0 = __ldg(t.leaf_lo + l0), P1 = __ldg(t.leaf_lo + l1 + 1);
-    if (FS) group_scan_f<DIM, K>(t, P0, P1, c, key, thr, thr_f);
-    else group_scan<DIM, K>(t, P0, P1, c, key, thr);
+    L.template scan<DIM>(t, P0, P1, c);
 
     // 2. their lowest common ancestor
     int C = ~l0;
     while (node_hi_pos(t, C) < P1) C = node_parent(t, C);
     const u64 mid_key = __shfl_sync(0xffffffffu, c.qkey, (gend - 1 - g0) >> 1);
-    group_search<DIM, K, FS>(t, C, l0, l1, mid_key, stack, c, key, thr, thr_f, status);
+    group_search<DIM>(t, C, l0, l1, mid_key, stack, c, L, status);
 
     // 3. climb (Algorithm 3) until no lane can improve from outside the node
     int node = C;
@@ -320,6 +465,7 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
         if (pbit >= t.cloud_bit) break; // never leave the cloud
         bool inside = true;
         if (c.live) {
+            const long long thr = L.climb_thr();
             // the node's cell: key bits >= pbit are the node's prefix
             const bool in_cell = allpts || ((c.qkey ^ __ldg(t.keys + node_lo_pos(t, node))) >> pbit) == 0;
             if (in_cell) {
@@ -334,22 +480,79 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
         }
         if (__all_sync(0xffffffffu, inside)) break;
         const int2 ch = __ldg(t.ichild + par);
-        group_search<DIM, K, FS>(t, ch.x == node ? ch.y : ch.x, l0, l1, mid_key, stack, c, key, thr, thr_f,
-                                 status);
+        group_search<DIM>(t, ch.x == node ? ch.y : ch.x, l0, l1, mid_key, stack, c, L, status);
         node = par;
         par = __ldg(t.iparent + par);
     }
 }
 
-template <int DIM, int K, bool FS>
-__global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *status)
+// SM-affine feed of warp groups.  The groups are cut into n_chunks contiguous
+// chunks (one per SM); a warp first takes groups, one atomic per group, from
+// the chunk of the SM it runs on, so the warps resident on an SM search
+// neighbouring groups and find one another's candidate points and boxes in
+// that SM's L1.  When its chunk is drained the warp steals single groups from
+// the other chunks (all counters read in one warp-wide pass, from L2) until
+// every chunk is drained.  A failed steal means that chunk ran out, so the
+// loop ends; the retry count is capped all the same (status ZD_ERR_INTERNAL).
+struct GroupFeed {
+    int home;      // the chunk of this warp's SM
+    bool stealing; // the home chunk is drained
+
+    __device__ __forceinline__ GroupFeed(const KnnArgs &a)
+    {
+        unsigned sm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        home = (int)(sm % (unsigned)a.n_chunks);
+        stealing = false;
+    }
+
+    __device__ __forceinline__ static bool take(const KnnArgs &a, int c, int64_t &g)
+    {
+        int gi = 0;
+        if ((threadIdx.x & 31) == 0) gi = atomicAdd(a.chunk_ctr + c, 1);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        g = (int64_t)c * a.chunk_len + gi;
+        return gi < a.chunk_len && g < a.n_groups;
+    }
+
+    // The next group of this warp, or -1.
+    __device__ __forceinline__ int64_t next(const KnnArgs &a, u32 *status)
+    {
+        const int lane = threadIdx.x & 31;
+        const int nch = a.n_chunks;
+        int64_t g;
+        if (!stealing) {
+            if (take(a, home, g)) return g;
+            stealing = true;
+        }
+        for (int tries = 0; tries < 4 * nch + 64; ++tries) {
+            int found = -1;
+            for (int base = 0; base < nch && found < 0; base += 32) {
+                const int c = (home + 1 + base + lane) % nch;
+                bool left = false;
+                if (base + lane < nch) {
+                    const int v = __ldcg(a.chunk_ctr + c);
+                    left = v < a.chunk_len && (int64_t)c * a.chunk_len + v < a.n_groups;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, left);
+                if (m) found = __shfl_sync(0xffffffffu, c, __ffs(m) - 1);
+            }
+            if (found < 0) return -1;
+            if (take(a, found, g)) return g;
+        }
+        if (lane == 0) set_status(status, ZD_ERR_INTERNAL);
+        return -1;
+    }
+};
+
+// One group: steps 1-3, then the answer of every lane (or the exact fallback).
+template <int DIM, int K, bool BAND>
+__device__ __forceinline__ void group_run(const KnnArgs &a, int64_t g, int *stack, int *band_col, u32 *status)
 {
+    typedef typename LaneOf<K, BAND>::type Lane;
     const TreeView &t = a.t;
-    __shared__ int s_stack[KNN_THREADS / 32][GROUP_STACK];
-    int *stack = s_stack[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    const int64_t g = ((int64_t)blockIdx.x * KNN_THREADS + threadIdx.x) >> 5;
     if (g >= a.n_groups || (a.group_count && g >= *a.group_count)) return; // whole warp
+    const int lane = threadIdx.x & 31;
     const bool allpts = a.allpts;
     const int64_t nq = allpts ? t.n : a.m;
     // the group: 32 consecutive queries in Morton order, never across clouds
@@ -379,22 +582,19 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
     c.sx = a.shift.x;
     c.sy = a.shift.y;
     c.sz = a.shift.z;
-    u64 key[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) key[j] = ~0ull;
-    long long thr = (long long)(c.sat - 1);
-    float thr_f = thr_float(thr);
+    Lane L;
+    L.init(c, band_col);
 
-    if (t.n > 0) group_traverse<DIM, K, FS>(t, a, c, key, thr, thr_f, g0, gend, allpts, stack, status);
-    (void)lane;
+    if (t.n > 0) group_traverse<DIM>(t, a, c, L, g0, gend, allpts, stack, status);
 
     if (!c.live) return;
     const int k = a.k;
+    u64 key[K];
+    bool saturated = !L.template finish<DIM>(t, c, key);
     // an entry among the first k that is missing (empty slots read as
     // saturated) or saturated: exact fallback
-    bool saturated = false; // static indices keep the list in registers
 #pragma unroll
-    for (int j = 0; j < K; ++j)
+    for (int j = 0; j < K; ++j) // static indices keep the list in registers
         saturated = saturated || (j < k && (key[j] >> c.idb) >= c.sat);
     if (saturated) {
         const int slot = atomicAdd(a.fix_count, 1);
@@ -417,11 +617,52 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
     }
 }
 
+// BAND: the tree has exact float copies (BandLane), else ExactLane.  With
+// a.chunk_ctr the launch is persistent and warps draw groups from the
+// SM-affine feed; without it warp w searches group w.
+template <int DIM, int K, bool BAND>
+__global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *status)
+{
+    constexpr int NW = KNN_THREADS / 32;
+    __shared__ int s_stack[NW][GROUP_STACK];
+    __shared__ int s_band[BAND ? NW : 1][BAND ? BandCap<K>::value : 1][32];
+    const int w = threadIdx.x >> 5;
+    int *stack = s_stack[w];
+    int *band_col = &s_band[BAND ? w : 0][0][threadIdx.x & 31];
+    if (!a.chunk_ctr) {
+        group_run<DIM, K, BAND>(a, ((int64_t)blockIdx.x * KNN_THREADS + threadIdx.x) >> 5, stack, band_col, status);
+        return;
+    }
+    GroupFeed feed(a);
+    for (int64_t g = feed.next(a, status); g >= 0; g = feed.next(a, status))
+        group_run<DIM, K, BAND>(a, g, stack, band_col, status);
+}
+
+// Persistent launch: as many blocks as fit on the device at once, but no
+// more warps than groups.
+template <int DIM, int K, bool BAND>
+void launch_group_kb(const KnnArgs &a, unsigned g, cudaStream_t s, u32 *st)
+{
+    if (a.chunk_ctr) {
+        static std::atomic<int> cached{0}; // resident blocks per SM of this instantiation
+        int occ = cached.load(std::memory_order_relaxed);
+        if (occ <= 0) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_knn_group<DIM, K, BAND>, KNN_THREADS, 0) !=
+                    cudaSuccess ||
+                occ <= 0)
+                occ = 1;
+            cached.store(occ, std::memory_order_relaxed);
+        }
+        g = (unsigned)std::min<int64_t>((int64_t)g, (int64_t)occ * a.n_chunks);
+    }
+    k_knn_group<DIM, K, BAND><<<g, KNN_THREADS, 0, s>>>(a, st);
+}
+
 template <int DIM, int K>
 void launch_group_k(const KnnArgs &a, unsigned g, cudaStream_t s, u32 *st)
 {
-    if (a.t.fpts) k_knn_group<DIM, K, true><<<g, KNN_THREADS, 0, s>>>(a, st);
-    else k_knn_group<DIM, K, false><<<g, KNN_THREADS, 0, s>>>(a, st);
+    if (a.t.fpts) launch_group_kb<DIM, K, true>(a, g, s, st);
+    else launch_group_kb<DIM, K, false>(a, g, s, st);
 }
 
 template <int DIM>
@@ -430,18 +671,23 @@ int launch_knn_group_dim(const KnnArgs &a, cudaStream_t s)
     if (a.n_groups <= 0) return ZD_OK;
     const unsigned g = (unsigned)((a.n_groups * 32 + KNN_THREADS - 1) / KNN_THREADS);
     u32 *st = status_word();
-    if (a.k <= 1) launch_group_k<DIM, 1>(a, g, s, st);
-    else if (a.k <= 2) launch_group_k<DIM, 2>(a, g, s, st);
-    else if (a.k <= 4) launch_group_k<DIM, 4>(a, g, s, st);
-    else if (a.k <= 5) launch_group_k<DIM, 5>(a, g, s, st);
-    else if (a.k <= 8) launch_group_k<DIM, 8>(a, g, s, st);
-    else if (a.k <= 10) launch_group_k<DIM, 10>(a, g, s, st);
-    else if (a.k <= 12) launch_group_k<DIM, 12>(a, g, s, st);
-    else if (a.k <= 16) launch_group_k<DIM, 16>(a, g, s, st);
-    else if (a.k <= 24) launch_group_k<DIM, 24>(a, g, s, st);
-    else if (a.k <= 28) launch_group_k<DIM, 28>(a, g, s, st);
-    else if (a.k <= 32) launch_group_k<DIM, 32>(a, g, s, st);
-    else launch_group_k<DIM, 40>(a, g, s, st);
+    KnnArgs b = a;
+    if (b.chunk_ctr) {
+        ZD_CUDA(cudaMemsetAsync(b.chunk_ctr, 0, sizeof(int) * (size_t)b.n_chunks, s));
+        b.chunk_len = (b.n_groups + b.n_chunks - 1) / b.n_chunks;
+    }
+    if (a.k <= 1) launch_group_k<DIM, 1>(b, g, s, st);
+    else if (a.k <= 2) launch_group_k<DIM, 2>(b, g, s, st);
+    else if (a.k <= 4) launch_group_k<DIM, 4>(b, g, s, st);
+    else if (a.k <= 5) launch_group_k<DIM, 5>(b, g, s, st);
+    else if (a.k <= 8) launch_group_k<DIM, 8>(b, g, s, st);
+    else if (a.k <= 10) launch_group_k<DIM, 10>(b, g, s, st);
+    else if (a.k <= 12) launch_group_k<DIM, 12>(b, g, s, st);
+    else if (a.k <= 16) launch_group_k<DIM, 16>(b, g, s, st);
+    else if (a.k <= 24) launch_group_k<DIM, 24>(b, g, s, st);
+    else if (a.k <= 28) launch_group_k<DIM, 28>(b, g, s, st);
+    else if (a.k <= 32) launch_group_k<DIM, 32>(b, g, s, st);
+    else launch_group_k<DIM, 40>(b, g, s, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

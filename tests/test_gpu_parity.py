@@ -309,6 +309,32 @@ def test_knn_far_from_the_origin(zd, oracle, dim, mapping):
     t.free()
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_knn_bands_wider_than_the_candidate_buffer(zd, oracle, mapping):
+    """Stacks of 50 identical points and lattice shells with many equal
+    distances: the band of near-equal estimates holds more candidates than a
+    lane buffers, so those queries take the exact fallback; every row must
+    still equal the oracle's (ties by id)."""
+    rng = np.random.default_rng(77)
+    stacks = np.repeat(rng.integers(0, 2 ** 18, size=(40, 3)), 50, axis=0)
+    g = np.stack(np.meshgrid(np.arange(14), np.arange(14), np.arange(14), indexing="ij"), -1).reshape(-1, 3)
+    lattice = g * 3 + 2 ** 19
+    rest = rng.integers(0, 2 ** 20, size=(20_000, 3))
+    pts = np.concatenate([stacks, lattice, rest]).astype(np.int32)
+    t = zd.zd_build(_t(pts), 16, 21)
+    ot = oracle.OracleTree(pts, 16, 21)
+    for k in (10, 24, 40):
+        idx, d2 = t.knn(k, mapping=mapping)
+        oi, od = ot.knn(k)
+        assert np.array_equal(d2.cpu().numpy(), od) and np.array_equal(idx.cpu().numpy(), oi), k
+    q = np.concatenate([stacks[::50] + 1, lattice[::7] + 1]).astype(np.int32)
+    idx, d2 = t.knn(12, queries=_t(q), mode=1, mapping=mapping)
+    oi, od = oracle.knn_brute(pts, 12, queries=q)
+    assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+    assert zd.zd_check() == 0
+    t.free()
+
+
 def test_knn_2d_uniform_workload(zd, oracle):
     """The 2D workload at its full size: n = 100,000, L = 16, k = 10."""
     from paper_2111_04182_gb300 import datagen
