@@ -101,13 +101,22 @@ __device__ __forceinline__ float thr_float(long long thr)
     return __fmul_ru(__ll2float_ru(thr), 1.0f + 1.0f / 1048576.0f);
 }
 
+// max(a, b, c) in one instruction (three-operand max.f32, sm_100 and later);
+// exact, like two fmaxf.
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 template <int DIM>
 __device__ __forceinline__ float box_d2f(const GroupCtx &c, float4 lo, float4 hi)
 {
-    const float cx = fmaxf(fmaxf(lo.x - c.fx, c.fx - hi.x), 0.f);
-    const float cy = fmaxf(fmaxf(lo.y - c.fy, c.fy - hi.y), 0.f);
+    const float cx = fmax3(lo.x - c.fx, c.fx - hi.x, 0.f);
+    const float cy = fmax3(lo.y - c.fy, c.fy - hi.y, 0.f);
     if (DIM == 3) {
-        const float cz = fmaxf(fmaxf(lo.z - c.fz, c.fz - hi.z), 0.f);
+        const float cz = fmax3(lo.z - c.fz, c.fz - hi.z, 0.f);
         return fmaf(cx, cx, fmaf(cy, cy, cz * cz));
     }
     return fmaf(cx, cx, cy * cy);
@@ -160,6 +169,7 @@ __device__ __forceinline__ bool axis_inside(long long q, long long lo, long long
 struct Probe {
     bool need;
     int a, b;
+    int bit; // an internal node's split bit
 };
 
 // ------------------------------------------------------------------------
@@ -193,10 +203,11 @@ struct ExactLane {
             r.a = ch.x;
             r.b = ch.y;
         }
+        r.bit = v >= 0 ? __ldg(t.ibit + v) : 0;
         return r;
     }
 
-    template <int DIM>
+    template <int DIM, bool SELF = false>
     __device__ __forceinline__ void scan(const TreeView &t, int a, int b, const GroupCtx &c)
     {
         for (int p = a; p < b; ++p) {
@@ -260,8 +271,7 @@ struct BandLane {
     float e[K];  // the K smallest estimates, ascending
     float thr;   // filter of candidates and boxes
     float cap;   // thr <= cap
-    int cnt;     // buffered candidates
-    bool over;   // the buffer overflowed: exact fallback
+    int cnt;     // buffered candidates; above CAP: the buffer overflowed (exact fallback)
     int *buf;    // this lane's column: entry s at buf[32 s]
 
     __device__ __forceinline__ void init(const GroupCtx &c, int *col)
@@ -269,9 +279,8 @@ struct BandLane {
 #pragma unroll
         for (int j = 0; j < K; ++j) e[j] = __int_as_float(0x7f800000);
         cap = thr_float((long long)(c.sat - 1));
-        thr = cap;
+        thr = c.live ? cap : -1.f; // a lane without a query accepts nothing
         cnt = 0;
-        over = false;
         buf = col;
     }
     __device__ __forceinline__ long long climb_thr() const { return __float2ll_ru(thr); }
@@ -283,7 +292,8 @@ struct BandLane {
         const float4 *fb = v < 0 ? t.flbox + 2 * (~v) : t.fibox + 2 * v;
         const float4 lo = __ldg(fb), hi = __ldg(fb + 1);
         Probe r;
-        r.need = c.live && box_d2f<DIM>(c, lo, hi) <= thr;
+        r.bit = v >= 0 ? __ldg(t.ibit + v) : 0; // issued beside the box loads
+        r.need = box_d2f<DIM>(c, lo, hi) <= thr;
         r.a = __float_as_int(lo.w);
         r.b = __float_as_int(hi.w);
         return r;
@@ -291,10 +301,8 @@ struct BandLane {
 
     __device__ __forceinline__ void take(float est, int p)
     {
-        if (!over) {
-            if (cnt < CAP) buf[32 * cnt++] = p;
-            else over = true;
-        }
+        if (cnt < CAP) buf[32 * cnt] = p;
+        cnt = min(cnt + 1, CAP + 1);
 #pragma unroll
         for (int j = K - 1; j > 0; --j) e[j] = fmaxf(e[j - 1], fminf(e[j], est));
         e[0] = fminf(e[0], est);
@@ -306,27 +314,28 @@ struct BandLane {
     template <int DIM>
     __device__ __forceinline__ void settle(const TreeView &t, const GroupCtx &c)
     {
-        if (!__any_sync(0xffffffffu, !over && cnt > CAP - 2)) return;
-        if (over) return;
+        if (!__any_sync(0xffffffffu, (unsigned)(cnt - (CAP - 1)) <= 1u)) return; // CAP - 1 or CAP
+        if (cnt > CAP) return;
         int w = 0;
         for (int s = 0; s < cnt; ++s) {
             const int p = buf[32 * s];
             if (est_d2f<DIM>(c, __ldg(t.fpts + p)) <= thr) buf[32 * w++] = p;
         }
-        cnt = w;
-        over = cnt > CAP - 2; // the band alone fills it
+        cnt = w > CAP - 2 ? CAP + 1 : w; // the band alone fills it: overflow
     }
 
-    // Sorted positions [a, b) for every lane, two candidates per step.
-    template <int DIM>
+    // Sorted positions [a, b) for every lane, two candidates per step.  SELF:
+    // the range may hold the lane's own point (the group's start leaves; the
+    // searches skip those).
+    template <int DIM, bool SELF = false>
     __device__ __forceinline__ void scan(const TreeView &t, int a, int b, const GroupCtx &c)
     {
         int p = a;
         for (; p + 1 < b; p += 2) {
             const float4 u = __ldg(t.fpts + p), v = __ldg(t.fpts + p + 1);
             const float eu = est_d2f<DIM>(c, u), ev = est_d2f<DIM>(c, v);
-            const bool pu = c.live && eu <= thr && p != c.self;
-            const bool pv = c.live && ev <= thr && p + 1 != c.self;
+            const bool pu = eu <= thr && (!SELF || p != c.self);
+            const bool pv = ev <= thr && (!SELF || p + 1 != c.self);
             if (__any_sync(0xffffffffu, pu || pv)) {
                 if (pu) take(eu, p);
                 if (pv && ev <= thr) take(ev, p + 1);
@@ -335,7 +344,7 @@ struct BandLane {
         }
         if (p < b) {
             const float eu = est_d2f<DIM>(c, __ldg(t.fpts + p));
-            const bool pu = c.live && eu <= thr && p != c.self;
+            const bool pu = eu <= thr && (!SELF || p != c.self);
             if (__any_sync(0xffffffffu, pu)) {
                 if (pu) take(eu, p);
                 settle<DIM>(t, c);
@@ -349,7 +358,7 @@ struct BandLane {
     {
 #pragma unroll
         for (int j = 0; j < K; ++j) out[j] = ~0ull;
-        if (over) return false;
+        if (cnt > CAP) return false;
         const float band = __fmul_ru(e[K - 1], 1.0f + 1.0f / 1048576.0f);
         for (int s = 0; s < cnt; ++s) {
             const int p = buf[32 * s];
@@ -394,7 +403,7 @@ __device__ __forceinline__ void group_search(const TreeView &t, int start, int l
                 if (v < 0) {
                     L.template scan<DIM>(t, pr.a, pr.b, c);
                 } else {
-                    const bool right_first = (mid_key >> __ldg(t.ibit + v)) & 1;
+                    const bool right_first = (mid_key >> pr.bit) & 1;
                     if (sp + 1 > GROUP_STACK) {
                         if (lane == 0) set_status(status, ZD_ERR_CUDA);
                         return;
@@ -449,19 +458,25 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
     }
     if (!ZD_DCHECK(l0 >= 0 && l0 <= l1 && node_in_range(t, ~l1), status)) return;
     const int P0 = __ldg(t.leaf_lo + l0), P1 = __ldg(t.leaf_lo + l1 + 1);
-    L.template scan<DIM>(t, P0, P1, c);
+    L.template scan<DIM, true>(t, P0, P1, c);
 
-    // 2. their lowest common ancestor
+    // 2. their lowest common ancestor (a node's end and parent loaded together)
     int C = ~l0;
-    while (node_hi_pos(t, C) < P1) C = node_parent(t, C);
+    int hi_pos = node_hi_pos(t, C), Cp = node_parent(t, C);
+    while (hi_pos < P1) {
+        C = Cp;
+        hi_pos = node_hi_pos(t, C);
+        Cp = node_parent(t, C);
+    }
     const u64 mid_key = __shfl_sync(0xffffffffu, c.qkey, (gend - 1 - g0) >> 1);
     group_search<DIM>(t, C, l0, l1, mid_key, stack, c, L, status);
 
     // 3. climb (Algorithm 3) until no lane can improve from outside the node
     int node = C;
-    int par = node_parent(t, C);
+    int par = Cp;
     while (par >= 0) {
-        const int pbit = __ldg(t.ibit + par);
+        const int pbit = __ldg(t.ibit + par); // the parent's fields, loaded together
+        const int2 ch = __ldg(t.ichild + par);
         if (pbit >= t.cloud_bit) break; // never leave the cloud
         bool inside = true;
         if (c.live) {
@@ -479,7 +494,6 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
             }
         }
         if (__all_sync(0xffffffffu, inside)) break;
-        const int2 ch = __ldg(t.ichild + par);
         group_search<DIM>(t, ch.x == node ? ch.y : ch.x, l0, l1, mid_key, stack, c, L, status);
         node = par;
         par = __ldg(t.iparent + par);
