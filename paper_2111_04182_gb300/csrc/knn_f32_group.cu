@@ -10,13 +10,19 @@ int launch_knn_group_f_3w(const KnnArgs &a, cudaStream_t s);
 int launch_knn_group_f_2n(const KnnArgs &a, cudaStream_t s);
 int launch_knn_group_f_2w(const KnnArgs &a, cudaStream_t s);
 
-// Warp groups, then the exact kernel for the queries whose band overflowed.
+// Warp groups, then the exact kernel for the queries whose band overflowed
+// the buffer.
 int launch_knn_group_f32(const KnnArgs &a, cudaStream_t s)
 {
     ZD_CUDA(cudaMemsetAsync(a.fix_count, 0, sizeof(int), s));
     if (a.n_groups > 0) {
-        if (a.t.dim == 3) ZD_TRY(a.k <= 16 ? launch_knn_group_f_3n(a, s) : launch_knn_group_f_3w(a, s));
-        else ZD_TRY(a.k <= 16 ? launch_knn_group_f_2n(a, s) : launch_knn_group_f_2w(a, s));
+        KnnArgs b = a;
+        if (b.chunk_ctr) { // the SM-affine group feed
+            ZD_CUDA(cudaMemsetAsync(b.chunk_ctr, 0, sizeof(int) * (size_t)b.n_chunks, s));
+            b.chunk_len = (b.n_groups + b.n_chunks - 1) / b.n_chunks;
+        }
+        if (b.t.dim == 3) ZD_TRY(b.k <= 16 ? launch_knn_group_f_3n(b, s) : launch_knn_group_f_3w(b, s));
+        else ZD_TRY(b.k <= 16 ? launch_knn_group_f_2n(b, s) : launch_knn_group_f_2w(b, s));
     }
     KnnArgs f = a;
     f.sel = a.fix_list;

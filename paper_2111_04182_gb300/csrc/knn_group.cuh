@@ -652,23 +652,25 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
         group_run<DIM, K, BAND>(a, g, stack, band_col, status);
 }
 
-// Persistent launch: as many blocks as fit on the device at once, but no
-// more warps than groups.
+// Blocks of a persistent launch of `kernel`: as many as fit on the device at
+// once (n_sm SMs), but no more than g (one warp per group).
+template <typename Kernel>
+unsigned persistent_blocks(Kernel kernel, unsigned g, int n_sm)
+{
+    static std::atomic<int> cached{0}; // resident blocks per SM (one per instantiation)
+    int occ = cached.load(std::memory_order_relaxed);
+    if (occ <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, KNN_THREADS, 0) != cudaSuccess || occ <= 0)
+            occ = 1;
+        cached.store(occ, std::memory_order_relaxed);
+    }
+    return (unsigned)std::min<int64_t>((int64_t)g, (int64_t)occ * n_sm);
+}
+
 template <int DIM, int K, bool BAND>
 void launch_group_kb(const KnnArgs &a, unsigned g, cudaStream_t s, u32 *st)
 {
-    if (a.chunk_ctr) {
-        static std::atomic<int> cached{0}; // resident blocks per SM of this instantiation
-        int occ = cached.load(std::memory_order_relaxed);
-        if (occ <= 0) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_knn_group<DIM, K, BAND>, KNN_THREADS, 0) !=
-                    cudaSuccess ||
-                occ <= 0)
-                occ = 1;
-            cached.store(occ, std::memory_order_relaxed);
-        }
-        g = (unsigned)std::min<int64_t>((int64_t)g, (int64_t)occ * a.n_chunks);
-    }
+    if (a.chunk_ctr) g = persistent_blocks(k_knn_group<DIM, K, BAND>, g, a.n_chunks);
     k_knn_group<DIM, K, BAND><<<g, KNN_THREADS, 0, s>>>(a, st);
 }
 

@@ -211,6 +211,30 @@ def test_float_knn_ties_and_duplicates(zd, oracle, mapping):
     t.free()
 
 
+@pytest.mark.parametrize("mapping", MAPPINGS)
+def test_float_knn_near_ties_at_the_kth_place(zd, oracle, mapping):
+    """A float lattice jittered by ~1e-6 of its spacing: distances that differ
+    in the 6th or 7th digit, closer than the fp32 estimates can separate, so
+    the k-th and (k+1)-th neighbours fall in one estimate band again and
+    again.  The exact (fp64, id) ranking of the band must pick the oracle's
+    k-th neighbour, whatever order the candidates were found in."""
+    rng = np.random.default_rng(81)
+    g = np.stack(np.meshgrid(*[np.arange(20)] * 3, indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    pts = (g * 0.5 + rng.normal(0, 5e-7, g.shape)).astype(np.float32)
+    t = zd.zd_build(_t(pts), 16, 21)
+    for k in (5, 8, 10, 16, 24):
+        idx, dist = t.knn(k, mapping=mapping)
+        assert zd.zd_check() == 0
+        bi, bd = oracle.knn_brute(pts, k)
+        assert np.array_equal(idx.cpu().numpy(), bi), k
+    q = (g[::3] * 0.5 + 0.25 + rng.normal(0, 5e-7, g[::3].shape)).astype(np.float32)
+    for mode in (1, 2):
+        idx, dist = t.knn(8, queries=_t(q), mode=mode, mapping=mapping)
+        bi, bd = oracle.knn_brute(pts, 8, queries=q)
+        assert np.array_equal(idx.cpu().numpy(), bi), mode
+    t.free()
+
+
 def test_float_knn_graph_three_starts(zd, oracle):
     from paper_2111_04182_gb300 import datagen
     _, b = datagen.warped_pair(np.random.default_rng(79), 10, 7000)
