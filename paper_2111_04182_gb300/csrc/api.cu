@@ -694,8 +694,16 @@ static int run_knn(const zd_tree *t, const int4 *q4, const u64 *qkeys, int64_t m
                        (allpts ? mode == ZD_SEARCH_LEAF
                                : ((mode == ZD_SEARCH_BIT && !t->cloud_off) || forest_ext));
     // beyond the register lists: one warp per query
-    if (k > KNN_MAX_K_GROUP || (k > KNN_MAX_K_THREAD && !group)) return launch_knn_wide(a, s);
-    if (!group) return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s);
+    const bool wide = k > KNN_MAX_K_GROUP || (k > KNN_MAX_K_THREAD && !group);
+    if (wide || !group) {
+        Mem wmem = mem_of(t, s);
+        Scratch<int> ctr(wmem, (size_t)sm_count()); // counters of the SM-affine query feed
+        if (!ctr.p) return ZD_ERR_OOM;
+        a.chunk_ctr = ctr.p;
+        a.n_chunks = sm_count();
+        if (wide) return launch_knn_wide(a, s); // one warp per query
+        return t->is_float ? launch_knn_f32(a, s) : launch_knn_i32(a, s); // one thread per query
+    }
     if (forest_ext) a.mode = ZD_SEARCH_BIT;
     Mem mem = mem_of(t, s);
     Scratch<int64_t> gpre(mem, forest_ext ? (size_t)t->n_clouds + 1 : 1);

@@ -37,9 +37,6 @@
 // only when their key carries the node's prefix, else the tight box.
 #pragma once
 
-#include <algorithm>
-#include <atomic>
-
 #include "knn_impl.cuh"
 
 namespace zdk {
@@ -500,65 +497,6 @@ __device__ __forceinline__ void group_traverse(const TreeView &t, const KnnArgs 
     }
 }
 
-// SM-affine feed of warp groups.  The groups are cut into n_chunks contiguous
-// chunks (one per SM); a warp first takes groups, one atomic per group, from
-// the chunk of the SM it runs on, so the warps resident on an SM search
-// neighbouring groups and find one another's candidate points and boxes in
-// that SM's L1.  When its chunk is drained the warp steals single groups from
-// the other chunks (all counters read in one warp-wide pass, from L2) until
-// every chunk is drained.  A failed steal means that chunk ran out, so the
-// loop ends; the retry count is capped all the same (status ZD_ERR_INTERNAL).
-struct GroupFeed {
-    int home;      // the chunk of this warp's SM
-    bool stealing; // the home chunk is drained
-
-    __device__ __forceinline__ GroupFeed(const KnnArgs &a)
-    {
-        unsigned sm;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
-        home = (int)(sm % (unsigned)a.n_chunks);
-        stealing = false;
-    }
-
-    __device__ __forceinline__ static bool take(const KnnArgs &a, int c, int64_t &g)
-    {
-        int gi = 0;
-        if ((threadIdx.x & 31) == 0) gi = atomicAdd(a.chunk_ctr + c, 1);
-        gi = __shfl_sync(0xffffffffu, gi, 0);
-        g = (int64_t)c * a.chunk_len + gi;
-        return gi < a.chunk_len && g < a.n_groups;
-    }
-
-    // The next group of this warp, or -1.
-    __device__ __forceinline__ int64_t next(const KnnArgs &a, u32 *status)
-    {
-        const int lane = threadIdx.x & 31;
-        const int nch = a.n_chunks;
-        int64_t g;
-        if (!stealing) {
-            if (take(a, home, g)) return g;
-            stealing = true;
-        }
-        for (int tries = 0; tries < 4 * nch + 64; ++tries) {
-            int found = -1;
-            for (int base = 0; base < nch && found < 0; base += 32) {
-                const int c = (home + 1 + base + lane) % nch;
-                bool left = false;
-                if (base + lane < nch) {
-                    const int v = __ldcg(a.chunk_ctr + c);
-                    left = v < a.chunk_len && (int64_t)c * a.chunk_len + v < a.n_groups;
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, left);
-                if (m) found = __shfl_sync(0xffffffffu, c, __ffs(m) - 1);
-            }
-            if (found < 0) return -1;
-            if (take(a, found, g)) return g;
-        }
-        if (lane == 0) set_status(status, ZD_ERR_INTERNAL);
-        return -1;
-    }
-};
-
 // One group: steps 1-3, then the answer of every lane (or the exact fallback).
 template <int DIM, int K, bool BAND>
 __device__ __forceinline__ void group_run(const KnnArgs &a, int64_t g, int *stack, int *band_col, u32 *status)
@@ -652,25 +590,10 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_group(KnnArgs a, u32 *statu
         group_run<DIM, K, BAND>(a, g, stack, band_col, status);
 }
 
-// Blocks of a persistent launch of `kernel`: as many as fit on the device at
-// once (n_sm SMs), but no more than g (one warp per group).
-template <typename Kernel>
-unsigned persistent_blocks(Kernel kernel, unsigned g, int n_sm)
-{
-    static std::atomic<int> cached{0}; // resident blocks per SM (one per instantiation)
-    int occ = cached.load(std::memory_order_relaxed);
-    if (occ <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, KNN_THREADS, 0) != cudaSuccess || occ <= 0)
-            occ = 1;
-        cached.store(occ, std::memory_order_relaxed);
-    }
-    return (unsigned)std::min<int64_t>((int64_t)g, (int64_t)occ * n_sm);
-}
-
 template <int DIM, int K, bool BAND>
 void launch_group_kb(const KnnArgs &a, unsigned g, cudaStream_t s, u32 *st)
 {
-    if (a.chunk_ctr) g = persistent_blocks(k_knn_group<DIM, K, BAND>, g, a.n_chunks);
+    if (a.chunk_ctr) g = persistent_blocks(k_knn_group<DIM, K, BAND>, KNN_THREADS, g, a.n_chunks);
     k_knn_group<DIM, K, BAND><<<g, KNN_THREADS, 0, s>>>(a, st);
 }
 

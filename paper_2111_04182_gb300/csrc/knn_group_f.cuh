@@ -370,7 +370,7 @@ template <int DIM, int K>
 void launch_group_f_k(const KnnArgs &a, cudaStream_t s, u32 *st)
 {
     unsigned g = (unsigned)((a.n_groups * 32 + KNN_THREADS - 1) / KNN_THREADS);
-    if (a.chunk_ctr) g = persistent_blocks(k_knn_group_f<DIM, K>, g, a.n_chunks);
+    if (a.chunk_ctr) g = persistent_blocks(k_knn_group_f<DIM, K>, KNN_THREADS, g, a.n_chunks);
     k_knn_group_f<DIM, K><<<g, KNN_THREADS, 0, s>>>(a, st);
 }
 

@@ -22,6 +22,8 @@
 // popped entry is re-tested against the k-th distance, which may have shrunk.
 #pragma once
 
+#include <algorithm>
+#include <atomic>
 #include <climits>
 
 #include "common.cuh"
@@ -243,6 +245,81 @@ __device__ __forceinline__ void scan_leaf(const TreeView &t, int leaf, int self,
     }
 }
 
+// SM-affine feed of work items (warp groups of queries, or single queries of
+// the warp-per-query kernel; n_groups of them).  The items are cut into
+// n_chunks contiguous chunks (one per SM); a warp first takes items, one
+// atomic per item, from the chunk of the SM it runs on, so the warps resident
+// on an SM search neighbouring queries (Morton order) and find one another's
+// candidate points and boxes in that SM's L1.  When its chunk is drained the warp steals single groups from
+// the other chunks (all counters read in one warp-wide pass, from L2) until
+// every chunk is drained.  A failed steal means that chunk ran out, so the
+// loop ends; the retry count is capped all the same (status ZD_ERR_INTERNAL).
+struct GroupFeed {
+    int home;      // the chunk of this warp's SM
+    bool stealing; // the home chunk is drained
+
+    __device__ __forceinline__ GroupFeed(const KnnArgs &a)
+    {
+        unsigned sm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        home = (int)(sm % (unsigned)a.n_chunks);
+        stealing = false;
+    }
+
+    __device__ __forceinline__ static bool take(const KnnArgs &a, int c, int64_t &g)
+    {
+        int gi = 0;
+        if ((threadIdx.x & 31) == 0) gi = atomicAdd(a.chunk_ctr + c, 1);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        g = (int64_t)c * a.chunk_len + gi;
+        return gi < a.chunk_len && g < a.n_groups;
+    }
+
+    // The next group of this warp, or -1.
+    __device__ __forceinline__ int64_t next(const KnnArgs &a, u32 *status)
+    {
+        const int lane = threadIdx.x & 31;
+        const int nch = a.n_chunks;
+        int64_t g;
+        if (!stealing) {
+            if (take(a, home, g)) return g;
+            stealing = true;
+        }
+        for (int tries = 0; tries < 4 * nch + 64; ++tries) {
+            int found = -1;
+            for (int base = 0; base < nch && found < 0; base += 32) {
+                const int c = (home + 1 + base + lane) % nch;
+                bool left = false;
+                if (base + lane < nch) {
+                    const int v = __ldcg(a.chunk_ctr + c);
+                    left = v < a.chunk_len && (int64_t)c * a.chunk_len + v < a.n_groups;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, left);
+                if (m) found = __shfl_sync(0xffffffffu, c, __ffs(m) - 1);
+            }
+            if (found < 0) return -1;
+            if (take(a, found, g)) return g;
+        }
+        if (lane == 0) set_status(status, ZD_ERR_INTERNAL);
+        return -1;
+    }
+};
+
+// Blocks of a persistent launch of `kernel` (`threads` per block): as many as
+// fit on the device at once (n_sm SMs), but no more than g.
+template <typename Kernel>
+unsigned persistent_blocks(Kernel kernel, int threads, unsigned g, int n_sm)
+{
+    static std::atomic<int> cached{0}; // resident blocks per SM (one per instantiation)
+    int occ = cached.load(std::memory_order_relaxed);
+    if (occ <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess || occ <= 0)
+            occ = 1;
+        cached.store(occ, std::memory_order_relaxed);
+    }
+    return (unsigned)std::min<int64_t>((int64_t)g, (int64_t)occ * n_sm);
+}
+
 // Node v names an existing node: internal 0 <= v < n_leaves - 1, or leaf
 // ~v < n_leaves (debug-build check).
 __device__ __forceinline__ bool node_in_range(const TreeView &t, int v)
@@ -444,11 +521,21 @@ __device__ __forceinline__ void knn_query(const KnnArgs &a, const int64_t qi, u3
     }
 }
 
+// One thread per query.  With a.chunk_ctr the launch is persistent and each
+// warp takes runs of 32 consecutive queries from the SM-affine feed.
 template <int DIM, int K, bool FLOAT>
 __global__ void __launch_bounds__(KNN_THREADS) k_knn(KnnArgs a, u32 *status)
 {
-    const int64_t qi = (int64_t)blockIdx.x * KNN_THREADS + threadIdx.x;
-    if (qi < a.m) knn_query<DIM, K, FLOAT>(a, qi, status);
+    if (!a.chunk_ctr) {
+        const int64_t qi = (int64_t)blockIdx.x * KNN_THREADS + threadIdx.x;
+        if (qi < a.m) knn_query<DIM, K, FLOAT>(a, qi, status);
+        return;
+    }
+    GroupFeed feed(a);
+    for (int64_t g = feed.next(a, status); g >= 0; g = feed.next(a, status)) {
+        const int64_t qi = g * 32 + (threadIdx.x & 31);
+        if (qi < a.m) knn_query<DIM, K, FLOAT>(a, qi, status);
+    }
 }
 
 // The same search for the sorted positions listed in a.sel (all-points mode).
@@ -463,8 +550,13 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_sel(KnnArgs a, u32 *status)
 template <int DIM, int K, bool FLOAT>
 void launch_knn_k(const KnnArgs &a, cudaStream_t s, u32 *st)
 {
-    if (a.sel) k_knn_sel<DIM, K, FLOAT><<<152 * 2, KNN_THREADS, 0, s>>>(a, st);
-    else k_knn<DIM, K, FLOAT><<<(unsigned)((a.m + KNN_THREADS - 1) / KNN_THREADS), KNN_THREADS, 0, s>>>(a, st);
+    if (a.sel) {
+        k_knn_sel<DIM, K, FLOAT><<<152 * 2, KNN_THREADS, 0, s>>>(a, st);
+        return;
+    }
+    unsigned g = (unsigned)((a.m + KNN_THREADS - 1) / KNN_THREADS);
+    if (a.chunk_ctr) g = persistent_blocks(k_knn<DIM, K, FLOAT>, KNN_THREADS, g, a.n_chunks);
+    k_knn<DIM, K, FLOAT><<<g, KNN_THREADS, 0, s>>>(a, st);
 }
 
 template <int DIM, bool FLOAT>
@@ -472,18 +564,26 @@ int launch_knn_dim(const KnnArgs &a, cudaStream_t s)
 {
     if (a.m <= 0 && !a.sel) return ZD_OK;
     u32 *st = status_word();
-    if (a.k <= 1) launch_knn_k<DIM, 1, FLOAT>(a, s, st);
-    else if (a.k <= 2) launch_knn_k<DIM, 2, FLOAT>(a, s, st);
-    else if (a.k <= 4) launch_knn_k<DIM, 4, FLOAT>(a, s, st);
-    else if (a.k <= 5) launch_knn_k<DIM, 5, FLOAT>(a, s, st);
-    else if (a.k <= 8) launch_knn_k<DIM, 8, FLOAT>(a, s, st);
-    else if (a.k <= 10) launch_knn_k<DIM, 10, FLOAT>(a, s, st);
-    else if (a.k <= 12) launch_knn_k<DIM, 12, FLOAT>(a, s, st);
-    else if (a.k <= 16) launch_knn_k<DIM, 16, FLOAT>(a, s, st);
-    else if (a.k <= 24) launch_knn_k<DIM, 24, FLOAT>(a, s, st);
-    else if (a.k <= 28) launch_knn_k<DIM, 28, FLOAT>(a, s, st);
-    else if (a.k <= 32) launch_knn_k<DIM, 32, FLOAT>(a, s, st);
-    else launch_knn_k<DIM, 40, FLOAT>(a, s, st); // the exact fallback of 40-wide groups
+    KnnArgs b = a;
+    if (b.sel) {
+        b.chunk_ctr = nullptr; // the exact fallback keeps its own loop
+    } else if (b.chunk_ctr) { // runs of 32 queries from the SM-affine feed
+        ZD_CUDA(cudaMemsetAsync(b.chunk_ctr, 0, sizeof(int) * (size_t)b.n_chunks, s));
+        b.n_groups = (b.m + 31) / 32;
+        b.chunk_len = (b.n_groups + b.n_chunks - 1) / b.n_chunks;
+    }
+    if (a.k <= 1) launch_knn_k<DIM, 1, FLOAT>(b, s, st);
+    else if (a.k <= 2) launch_knn_k<DIM, 2, FLOAT>(b, s, st);
+    else if (a.k <= 4) launch_knn_k<DIM, 4, FLOAT>(b, s, st);
+    else if (a.k <= 5) launch_knn_k<DIM, 5, FLOAT>(b, s, st);
+    else if (a.k <= 8) launch_knn_k<DIM, 8, FLOAT>(b, s, st);
+    else if (a.k <= 10) launch_knn_k<DIM, 10, FLOAT>(b, s, st);
+    else if (a.k <= 12) launch_knn_k<DIM, 12, FLOAT>(b, s, st);
+    else if (a.k <= 16) launch_knn_k<DIM, 16, FLOAT>(b, s, st);
+    else if (a.k <= 24) launch_knn_k<DIM, 24, FLOAT>(b, s, st);
+    else if (a.k <= 28) launch_knn_k<DIM, 28, FLOAT>(b, s, st);
+    else if (a.k <= 32) launch_knn_k<DIM, 32, FLOAT>(b, s, st);
+    else launch_knn_k<DIM, 40, FLOAT>(b, s, st); // the exact fallback of 40-wide groups
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

@@ -389,8 +389,12 @@ __global__ void __launch_bounds__(32 * WIDE_WARPS, R >= 3 ? 6 : 8) k_knn_wide(Kn
     const int nl = __ldg(t.meta);
     const int root = nl > 1 ? 0 : ~0;
 
-    for (int64_t qi = (int64_t)blockIdx.x * WIDE_WARPS + warp; qi < a.m;
-         qi += (int64_t)gridDim.x * WIDE_WARPS) {
+    // queries from the SM-affine feed (persistent launch, a.chunk_ctr), else
+    // a grid-stride loop
+    GroupFeed feed(a);
+    for (int64_t qi = a.chunk_ctr ? feed.next(a, status) : (int64_t)blockIdx.x * WIDE_WARPS + warp;
+         qi >= 0 && qi < a.m;
+         qi = a.chunk_ctr ? feed.next(a, status) : qi + (int64_t)gridDim.x * WIDE_WARPS) {
         __syncwarp();
         WideQuery<DIM, R, FLOAT> w(t, a.k, lane, s_bufd[warp], s_bufi[warp], s_pd[warp], s_pi[warp], s_sn[warp],
                                    s_sd[warp]);
@@ -490,15 +494,29 @@ __global__ void __launch_bounds__(32 * WIDE_WARPS, R >= 3 ? 6 : 8) k_knn_wide(Kn
     }
 }
 
+template <int DIM, int R, bool FLOAT>
+void launch_wide_r(const KnnArgs &a, unsigned grid, cudaStream_t s, u32 *st)
+{
+    if (a.chunk_ctr) grid = persistent_blocks(k_knn_wide<DIM, R, FLOAT>, 32 * WIDE_WARPS, grid, a.n_chunks);
+    k_knn_wide<DIM, R, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
+}
+
 template <int DIM, bool FLOAT>
 int launch_knn_wide_dim(const KnnArgs &a, cudaStream_t s)
 {
     if (a.m <= 0) return ZD_OK;
     u32 *st = status_word();
+    KnnArgs b = a;
     const unsigned grid = grid_for(a.m, WIDE_WARPS, 152 * 64);
-    if (a.k <= 64) k_knn_wide<DIM, 2, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
-    else if (a.k <= 96) k_knn_wide<DIM, 3, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
-    else k_knn_wide<DIM, 4, FLOAT><<<grid, 32 * WIDE_WARPS, 0, s>>>(a, st);
+    if (b.chunk_ctr) { // one query per feed item
+        ZD_CUDA(cudaMemsetAsync(b.chunk_ctr, 0, sizeof(int) * (size_t)b.n_chunks, s));
+        b.n_groups = b.m;
+        b.chunk_len = (b.m + b.n_chunks - 1) / b.n_chunks;
+    }
+    const unsigned want = (unsigned)std::min<int64_t>((a.m + WIDE_WARPS - 1) / WIDE_WARPS, 1 << 30);
+    if (a.k <= 64) launch_wide_r<DIM, 2, FLOAT>(b, b.chunk_ctr ? want : grid, s, st);
+    else if (a.k <= 96) launch_wide_r<DIM, 3, FLOAT>(b, b.chunk_ctr ? want : grid, s, st);
+    else launch_wide_r<DIM, 4, FLOAT>(b, b.chunk_ctr ? want : grid, s, st);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }
