@@ -16,7 +16,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUITES = ["tests/test_gpu_parity.py", "tests/test_gpu_dynamic.py", "tests/test_gpu_batched.py",
-          "tests/test_gpu_large_k.py", "tests/test_gpu_backward.py", "tests/test_gpu_failure.py"]
+          "tests/test_gpu_large_k.py", "tests/test_gpu_backward.py", "tests/test_gpu_failure.py",
+          "tests/test_gpu_small_updates.py"]
 
 
 @pytest.mark.skipif(os.environ.get("ZD_TEST_DEBUG_BUILD") != "1", reason="set ZD_TEST_DEBUG_BUILD=1")
