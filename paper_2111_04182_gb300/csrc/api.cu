@@ -800,12 +800,13 @@ extern "C" int zd_knn_batched(const zd_tree *t, const void *d_queries, const int
 namespace zdk {
 int update_insert(const TreeView &v, const u64 *keys, const int4 *pts, int64_t n, const void *d_pts,
                   int64_t b, int dim, int B, const uint32_t *shift, int key_bits, int32_t next_id,
-                  u64 *keys_out, int4 *pts_out, u32 *live, int32_t *d_new_ids, Mem &mem);
+                  u64 *keys_out, int4 *pts_out, u32 *live, int32_t *d_new_ids, Mem &mem, float4 *fpts_out);
 int update_delete_mark(u32 *live, u32 *marked, int64_t id_cap, const int32_t *ids, int64_t b, Mem &mem,
                        int *result);
 int update_delete_unmark(u32 *live, u32 *marked, int64_t id_cap, const int32_t *ids, int64_t b, cudaStream_t s);
 int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *live, u32 *marked,
-                          const int32_t *ids, int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem);
+                          const int32_t *ids, int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem,
+                          float4 *fpts_out, uint3 fsh);
 int update_live_bits(u32 *live, int64_t a, int64_t z, int set, cudaStream_t s);
 } // namespace zdk
 
@@ -838,19 +839,26 @@ static int flat_insert(zd_tree *t, const void *d_pts, int64_t b, int64_t first_i
     // the previous call's device errors must not be mistaken for this one's
     int prior = zd_check(s);
     if (prior != ZD_OK) return prior;
+    // the merge writes the float copy of the merged points as well (the
+    // copy has one buffer: a rejected batch restores it from the old points)
     int r = update_insert(view_of(t), t->keys, t->pts, t->n, d_pts, b, t->p.dim, t->B, t->p.shift,
-                          t->key_bits, (int32_t)first_id, t->keys2, t->pts2, t->alive, d_new_ids, mem);
-    if (r != ZD_OK) return r;
+                          t->key_bits, (int32_t)first_id, t->keys2, t->pts2, t->alive, d_new_ids, mem, t->fpts);
+    if (r != ZD_OK) {
+        if (t->fpts) launch_fpts(t->pts, t->n, t->fpts, topo_of(t).fshift, s);
+        return r;
+    }
     int st = zd_check(s);
     if (st != ZD_OK) {
         // nothing was committed: the new ids are released again
         update_live_bits(t->alive, first_id, first_id + b, 0, s);
+        if (t->fpts) launch_fpts(t->pts, t->n, t->fpts, topo_of(t).fshift, s);
         return st;
     }
     std::swap(t->keys, t->keys2);
     std::swap(t->pts, t->pts2);
     t->n += b;
-    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), mem));
+    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), mem,
+                          /*fpts_ready=*/t->fpts != nullptr));
     return mem.failed ? ZD_ERR_OOM : ZD_OK;
 }
 
@@ -869,12 +877,14 @@ static int flat_delete(zd_tree *t, const int32_t *d_ids, int64_t b, cudaStream_t
         ZD_CUDA(cudaStreamSynchronize(s));
         return result;
     }
+    // validated above: the compaction writes the float copy too
     ZD_TRY(update_delete_compact(t->keys, t->pts, t->n, live, marked, d_ids, b, t->id_cap, t->keys2, t->pts2,
-                                 mem));
+                                 mem, t->fpts, topo_of(t).fshift));
     std::swap(t->keys, t->keys2);
     std::swap(t->pts, t->pts2);
     t->n -= b;
-    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), mem));
+    ZD_TRY(build_topology(t->keys, t->pts, t->n, t->p.leaf_size, t->p.dim, 0, 64, topo_of(t), mem,
+                          /*fpts_ready=*/t->fpts != nullptr));
     int st = zd_check(s);
     if (st != ZD_OK) return st;
     return mem.failed ? ZD_ERR_OOM : ZD_OK;

@@ -19,14 +19,6 @@
 
 namespace zdk {
 
-// Exact float copy of an integer point: the shifted coordinates (c + shift
-// lies in [0, 2^B), B <= 24), id bits kept in w.
-__device__ __forceinline__ float4 shifted_float4(int4 p, uint3 sh)
-{
-    return make_float4((float)((unsigned)p.x + sh.x), (float)((unsigned)p.y + sh.y),
-                       (float)((unsigned)p.z + sh.z), __int_as_float(p.w));
-}
-
 // ----------------------------------------------------------------- gather
 template <int DIM>
 __global__ void __launch_bounds__(256) k_gather(const int32_t *__restrict__ pts, int64_t n,
@@ -463,6 +455,13 @@ int launch_group_starts(const int64_t *cloud_off, int64_t n_clouds, int64_t n_gr
     if (n_groups > 0)
         k_group_starts<<<grid_for(n_groups, 256, 152 * 16), 256, 0, s>>>(cloud_off, gpre, n_clouds, n_groups,
                                                                         group_start);
+    ZD_CUDA(cudaGetLastError());
+    return ZD_OK;
+}
+
+int launch_fpts(const int4 *pts, int64_t n, float4 *fpts, uint3 shift, cudaStream_t s)
+{
+    if (n > 0) k_fpts<<<grid_for(n, 256, 152 * 32), 256, 0, s>>>(pts, n, fpts, shift);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
 }

@@ -47,6 +47,14 @@ __device__ __forceinline__ void set_status(u32 *status, int code)
 // Host: address of this device's status word (looked up once per device).
 u32 *status_word();
 
+// Exact float copy of an integer point: the shifted coordinates (c + shift
+// lies in [0, 2^B), B <= 24), id bits kept in w.
+__device__ __forceinline__ float4 shifted_float4(int4 p, uint3 sh)
+{
+    return make_float4((float)((unsigned)p.x + sh.x), (float)((unsigned)p.y + sh.y),
+                       (float)((unsigned)p.z + sh.z), __int_as_float(p.w));
+}
+
 // Host: this device's number of SMs (looked up once per device).
 int sm_count();
 
@@ -203,7 +211,10 @@ struct TopoBuffers {
 // Boundaries whose highest differing key bit is >= force_bit (the cloud id
 // bits of a forest; 64 for one tree) always separate leaves, so every
 // cloud's subtree is that cloud's own canonical tree.
-// fpts_ready: b.fpts was already written (by the gather).
+// Write the float copy of sorted integer points (shifted_float4).
+int launch_fpts(const int4 *pts, int64_t n, float4 *fpts, uint3 shift, cudaStream_t s);
+
+// fpts_ready: b.fpts was already written (by the gather or an update).
 int build_topology(const u64 *keys, const int4 *pts, int64_t n, int leaf_size, int dim,
                    int is_float, int force_bit, const TopoBuffers &b, Mem &mem, bool fpts_ready = false);
 

@@ -41,7 +41,8 @@ constexpr int MERGE_TILE = 1024;
 // by (key, id).
 __global__ void __launch_bounds__(256) k_merge_old(const u64 *__restrict__ keys, const int4 *__restrict__ pts,
                                                    int64_t n, const u64 *__restrict__ bkeys, int64_t b,
-                                                   u64 *__restrict__ keys_out, int4 *__restrict__ pts_out)
+                                                   u64 *__restrict__ keys_out, int4 *__restrict__ pts_out,
+                                                   float4 *__restrict__ fpts_out, uint3 fsh)
 {
     __shared__ int64_t s_rng[2];
     const int64_t i0 = (int64_t)blockIdx.x * MERGE_TILE;
@@ -56,22 +57,27 @@ __global__ void __launch_bounds__(256) k_merge_old(const u64 *__restrict__ keys,
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const u64 key = keys[i];
         const int64_t c = lower_bound_u64(bkeys, lo, hi, key);
+        const int4 p = pts[i];
         keys_out[i + c] = key;
-        pts_out[i + c] = pts[i];
+        pts_out[i + c] = p;
+        if (fpts_out) fpts_out[i + c] = shifted_float4(p, fsh);
     }
 }
 
 __global__ void __launch_bounds__(256) k_merge_new(const u64 *__restrict__ keys, int64_t n,
                                                    const u64 *__restrict__ bkeys, const int4 *__restrict__ bpts,
                                                    int64_t b, u64 *__restrict__ keys_out,
-                                                   int4 *__restrict__ pts_out)
+                                                   int4 *__restrict__ pts_out, float4 *__restrict__ fpts_out,
+                                                   uint3 fsh)
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < b;
          j += (int64_t)gridDim.x * blockDim.x) {
         const u64 key = bkeys[j];
         const int64_t c = upper_bound_u64(keys, 0, n, key);
+        const int4 p = bpts[j];
         keys_out[j + c] = key;
-        pts_out[j + c] = bpts[j];
+        pts_out[j + c] = p;
+        if (fpts_out) fpts_out[j + c] = shifted_float4(p, fsh);
     }
 }
 
@@ -105,8 +111,9 @@ int update_live_bits(u32 *live, int64_t a, int64_t z, int set, cudaStream_t s)
 
 int update_insert(const TreeView &v, const u64 *keys, const int4 *pts, int64_t n, const void *d_pts,
                   int64_t b, int dim, int B, const uint32_t *shift, int key_bits, int32_t next_id,
-                  u64 *keys_out, int4 *pts_out, u32 *live, int32_t *d_new_ids, Mem &mem)
+                  u64 *keys_out, int4 *pts_out, u32 *live, int32_t *d_new_ids, Mem &mem, float4 *fpts_out)
 {
+    const uint3 fsh = make_uint3(shift ? shift[0] : 0u, shift ? shift[1] : 0u, shift ? shift[2] : 0u);
     (void)v;
     cudaStream_t s = mem.s;
     const int npasses = (key_bits + RADIX_BITS - 1) / RADIX_BITS;
@@ -123,8 +130,9 @@ int update_insert(const TreeView &v, const u64 *keys, const int4 *pts, int64_t n
     if (d_new_ids) k_iota<<<grid_for(b, 256, 4096), 256, 0, s>>>(d_new_ids, b, next_id);
     if (n > 0)
         k_merge_old<<<(unsigned)((n + MERGE_TILE - 1) / MERGE_TILE), 256, 0, s>>>(keys, pts, n, bkeys.p, b,
-                                                                               keys_out, pts_out);
-    k_merge_new<<<grid_for(b, 256, 152 * 16), 256, 0, s>>>(keys, n, bkeys.p, bpts.p, b, keys_out, pts_out);
+                                                                               keys_out, pts_out, fpts_out, fsh);
+    k_merge_new<<<grid_for(b, 256, 152 * 16), 256, 0, s>>>(keys, n, bkeys.p, bpts.p, b, keys_out, pts_out,
+                                                            fpts_out, fsh);
     k_live_bits<<<grid_for(b, 256, 4096), 256, 0, s>>>(live, next_id, next_id + b, 1);
     ZD_CUDA(cudaGetLastError());
     return ZD_OK;
@@ -262,7 +270,8 @@ __global__ void __launch_bounds__(CMP_THREADS) k_keep_scatter(const u64 *__restr
                                                              const unsigned char *__restrict__ keep,
                                                              const int *__restrict__ off,
                                                              u64 *__restrict__ keys_out,
-                                                             int4 *__restrict__ pts_out)
+                                                             int4 *__restrict__ pts_out,
+                                                             float4 *__restrict__ fpts_out, uint3 fsh)
 {
     __shared__ int s_cnt[CMP_ITEMS][CMP_THREADS / 32];
     const int64_t t0 = (int64_t)blockIdx.x * CMP_TILE;
@@ -295,14 +304,17 @@ __global__ void __launch_bounds__(CMP_THREADS) k_keep_scatter(const u64 *__restr
         if (ball[it] & (1u << lane)) {
             const int64_t i = t0 + it * CMP_THREADS + threadIdx.x;
             const int64_t pos = base + before + __popc(ball[it] & lt);
+            const int4 p = pts[i];
             keys_out[pos] = keys[i];
-            pts_out[pos] = pts[i];
+            pts_out[pos] = p;
+            if (fpts_out) fpts_out[pos] = shifted_float4(p, fsh);
         }
     }
 }
 
 int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *live, u32 *marked,
-                          const int32_t *ids, int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem)
+                          const int32_t *ids, int64_t b, int64_t id_cap, u64 *keys_out, int4 *pts_out, Mem &mem,
+                          float4 *fpts_out, uint3 fsh)
 {
     cudaStream_t s = mem.s;
     const int64_t nb = (n + CMP_TILE - 1) / CMP_TILE;
@@ -312,7 +324,8 @@ int update_delete_compact(const u64 *keys, const int4 *pts, int64_t n, u32 *live
     if (nb > 0) {
         k_keep_flags<<<(unsigned)nb, CMP_THREADS, 0, s>>>(pts, n, marked, keep.p, count.p);
         k_excl_scan<<<1, 1024, 0, s>>>(count.p, nb);
-        k_keep_scatter<<<(unsigned)nb, CMP_THREADS, 0, s>>>(keys, pts, n, keep.p, count.p, keys_out, pts_out);
+        k_keep_scatter<<<(unsigned)nb, CMP_THREADS, 0, s>>>(keys, pts, n, keep.p, count.p, keys_out, pts_out,
+                                                            fpts_out, fsh);
     }
     k_unmark<<<grid_for(b, 256, 4096), 256, 0, s>>>(live, marked, id_cap, ids, b, 1);
     ZD_CUDA(cudaGetLastError());

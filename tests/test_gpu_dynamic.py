@@ -113,5 +113,12 @@ def test_update_errors_leave_tree_unchanged(zd, oracle):
     oset.delete([10, 11])
     _same_tree(t, oset)
     assert t.info()["n"] == 4998
+    # the all-points search reads the float copy of the points, which a
+    # rejected large insert has to leave (or put back) as it was
+    idx, d2 = t.knn(4)
+    oi, od, oids = oset.tree().knn(4)  # rows in sorted order, with their ids
+    rows = oids.astype(np.int64)
+    assert np.array_equal(idx.cpu().numpy()[rows], oi) and np.array_equal(d2.cpu().numpy()[rows], od)
+    assert zd.zd_check() == zd.ZD_OK
     t.free()
     assert zd.zd_check() == 0
