@@ -359,6 +359,34 @@ def test_knn_bands_wider_than_the_candidate_buffer(zd, oracle, mapping):
     t.free()
 
 
+@pytest.mark.parametrize("bits", [24, 25])
+def test_knn_at_the_float_copy_limit(zd, oracle, bits):
+    """2D points spread over [0, 2^bits): B = 24 is the widest grid with exact
+    float copies (the warp groups' band lanes, differences and squares at the
+    edge of fp32's exact integers), B = 25 the narrowest without them (exact
+    int64 lanes).  Clustered, with duplicates; all points and external
+    queries against the oracle."""
+    rng = np.random.default_rng(60 + bits)
+    hi = 2 ** bits - 1
+    c = rng.integers(0, hi, size=(8, 2))
+    pts = np.clip(c[rng.integers(0, 8, 30_000)] + rng.normal(0, 2 ** (bits - 6), (30_000, 2)), 0, hi)
+    pts = pts.astype(np.int64)
+    pts[:64] = [[0, 0], [hi, hi], [0, hi], [hi, 0]] * 16  # the grid's corners, repeated
+    pts = pts.astype(np.int32)
+    t = zd.zd_build(_t(pts), 16, bits)
+    ot = oracle.OracleTree(pts, 16, bits)
+    for k in (3, 10, 16):
+        idx, d2 = t.knn(k)
+        oi, od = ot.knn(k)
+        assert np.array_equal(d2.cpu().numpy(), od) and np.array_equal(idx.cpu().numpy(), oi), k
+    q = rng.integers(0, hi, size=(8_000, 2)).astype(np.int32)
+    idx, d2 = t.knn(5, queries=_t(q), mode=1)
+    oi, od = oracle.knn_brute(pts, 5, queries=q)
+    assert np.array_equal(idx.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+    assert zd.zd_check() == 0
+    t.free()
+
+
 def test_knn_2d_uniform_workload(zd, oracle):
     """The 2D workload at its full size: n = 100,000, L = 16, k = 10."""
     from paper_2111_04182_gb300 import datagen
