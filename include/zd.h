@@ -33,7 +33,10 @@
  *   ids in order; deleted ids are never reused.
  * - A `const zd_tree*` may be searched from several streams at once (the
  *   paper's queries run concurrently on a shared tree, Sec. 1); updates need
- *   exclusive access.
+ *   exclusive access.  A search launches persistent kernels (as many blocks
+ *   as fit on the device) whose warps take work from per-SM queues that the
+ *   call allocates for itself; no warp waits for another, so concurrent
+ *   searches stay correct while they share the SMs.
  */
 #ifndef ZD_H
 #define ZD_H
